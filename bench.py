@@ -1,0 +1,327 @@
+"""Benchmark of blocked Floyd-Warshall APSP on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--dtype f32|i32] [--n 16384] [--no-cpu-baseline]
+
+Metric: relaxations per second, n^3 / t, for one all-pairs shortest-paths
+solve of a dense complete directed graph with fp32 weights uniform in (0,1]
+at n = 16384 (the size of the paper's headline run).  A step is one solve:
+restore the input matrix (device-to-device copy of the resident pristine
+input) and run every stage of Fig. 2 in place.  The matrix (1 GiB) is larger
+than L2, so no explicit flush is needed between steps.
+
+One JSON line on rank 0.  With N > 1 (torchrun) every rank solves its own
+matrix: a single solve does not split across GPUs without a per-stage panel
+exchange, so the multi-GPU form is independent replicas (weak scaling).
+
+--impl reference times the oracle (the plain Fig. 1 triple loop in FP64,
+single thread, on the host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PAPER_SECONDS_N16384 = 53.06  # Tesla C1060, fp32, n = 16384 (Sec. 1)
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "i32"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--kblock", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload_name(dtype, n):
+    if dtype == "f32":
+        return f"dense complete directed graph, fp32 weights uniform in (0,1], n={n}"
+    return f"directed graph, edge probability 0.3, int32 weights uniform in [1,1000], n={n}"
+
+
+def _make_input(dtype, n, seed):
+    from paper_1001_4108_gb300 import inputs
+    if dtype == "f32":
+        return inputs.dense_f32(n, seed=seed)
+    return inputs.int_graph(n, 0.3, 1, 1000, seed=seed)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(dtype: str, n_sample: int = 2048):
+    """The oracle as it stands (Fig. 1 triple loop, FP64 / int64, one thread)
+    on a bounded sample of the workload."""
+    import oracle
+    w = _make_input(dtype, n_sample, seed=0)
+    oracle.build()
+    t0 = time.perf_counter()
+    if dtype == "f32":
+        oracle.fw_f64(w)
+    else:
+        oracle.fw_int32_conv(w)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample ** 3 / dt, "unit": "relaxations/s", "cores": 1, "kind": "oracle",
+            "sample": f"one Fig. 1 solve ({'FP64' if dtype == 'f32' else 'int64'}, single thread) of the same "
+                      f"generator at n={n_sample} ({dt:.2f} s); relaxations/s scale as n^3 / t",
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(a):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n_sample = 1024
+    w = _make_input(a.dtype, n_sample, seed=0)
+    f = oracle.fw_f64 if a.dtype == "f32" else oracle.fw_int32_conv
+    for _ in range(a.warmup):
+        f(w)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        f(w)
+    dt = time.perf_counter() - t0
+    value = a.steps * n_sample ** 3 / dt
+    line = {
+        "impl": "reference", "metric": "relaxations/s (n^3/t)", "value": value, "unit": "relaxations/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if a.dtype == "f32" else "int64", "data": "synthetic",
+        "config": {"workload": _workload_name(a.dtype, a.n), "sample_n": n_sample},
+        "cpu_baseline": {"value": value, "unit": "relaxations/s", "cores": 1, "kind": "oracle",
+                         "sample": f"Fig. 1 triple loop, single thread, n={n_sample} per step"},
+        "e2e": {"value": value, "unit": "relaxations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1001_4108_gb300 import binding, build
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    L = binding.lib()
+    n = a.n
+    es = 4
+    cfg = binding.query_config(n, binding.APSP_F32 if a.dtype == "f32" else binding.APSP_I32, a.kblock)
+    R = cfg.rounds
+    w = _make_input(a.dtype, n, seed=rank)
+    pristine = torch.from_numpy(w).cuda()
+    work = torch.empty_like(pristine)
+    stream = torch.cuda.current_stream()
+
+    nev = 4 * R
+    step_events = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(a.steps)]
+
+    def step(events=None):
+        work.copy_(pristine)
+        binding.apsp_fw(work, kblock=a.kblock, events=events, flags=binding.FLAG_NO_GRAPH)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert binding.device_error() == 0
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(a.steps):
+        step(step_events[k])   # per-phase events recorded on the launching stream
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    p3_ms, p1_ms, p2_ms = [], [], []
+    for events in step_events:
+        for r in range(R):
+            p1_ms.append(events[4 * r].elapsed_time(events[4 * r + 1]))
+            p2_ms.append(events[4 * r + 1].elapsed_time(events[4 * r + 2]))
+            if R > 1 and (r + 1) * cfg.kblock <= n:   # full k-block: the TMA phase-3 kernel
+                p3_ms.append(events[4 * r + 2].elapsed_time(events[4 * r + 3]))
+    torch.cuda.synchronize()
+    total_ms = t_start.elapsed_time(t_end)
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        dist.barrier()
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    assert binding.device_error() == 0
+
+    relax_per_step = float(n) ** 3
+    value = world * a.steps * relax_per_step / (total_ms * 1e-3)
+
+    # e2e: the host entry point (pinned host matrix -> H2D -> solve -> D2H)
+    e2e = None
+    if a.e2e_steps > 0:
+        host = torch.from_numpy(w).pin_memory()
+        src = host.clone()
+        for _ in range(2):  # warm-up: allocates the device stage, captures the graph
+            host.copy_(src)
+            binding.apsp_fw_host(host)
+        tot = 0.0
+        for _ in range(a.e2e_steps):
+            host.copy_(src)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            binding.apsp_fw_host(host)
+            tot += time.perf_counter() - t0
+        e2e = {"value": world * a.e2e_steps * relax_per_step / tot, "unit": "relaxations/s",
+               "h2d_bytes_per_step": n * n * es, "d2h_bytes_per_step": n * n * es,
+               "ms_per_step": tot / a.e2e_steps * 1e3}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = _peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # min-plus ALU roofline: every SM issues 4 warp-instructions (128 lanes)
+    # per clock; one relaxation needs at least one instruction (DPX add-min
+    # for int32, half of a packed f32x2 add + half of a three-input min for
+    # fp32), so the ceiling is SMs x f_max x 128 relaxations per second.
+    peak = sms * sm_max * 1e6 * 128
+    p3_relax = float(cfg.phase3_relax_per_round)
+    p3_mean_s = statistics.mean(p3_ms) * 1e-3 if p3_ms else float("nan")
+    achieved = p3_relax / p3_mean_s
+    hbm_bytes = 2.0 * es * (n - cfg.kblock) ** 2  # C tile read + write per phase-3 launch
+    line = {
+        "metric": "relaxations/s (n^3/t)", "value": value, "unit": "relaxations/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / (float(a.n) ** 3 / PAPER_SECONDS_N16384) if a.n == 16384 and a.dtype == "f32" else None,
+        "dtype": a.dtype, "data": "synthetic",
+        "config": {"workload": _workload_name(a.dtype, n), "n": n, "kblock": cfg.kblock, "rounds": R,
+                   "l2": "inputs larger than L2 (matrix %.2f GiB)" % (n * n * es / 2 ** 30),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": "fw_phase3_tma", "achieved": achieved, "peak": peak,
+                     "unit": "relaxations/s", "frac": achieved / peak,
+                     "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz ({peak_kind} max clock) x 128 lanes / 1 instr",
+                     "traffic": None,
+                     "algorithmic_hbm_GBps": hbm_bytes / p3_mean_s / 1e9,
+                     "hbm_peak_GBps": peaks.get("hbm_gbs"),
+                     "phase3_ms_mean": p3_mean_s * 1e3,
+                     "phase1_ms_mean": statistics.mean(p1_ms), "phase2_ms_mean": statistics.mean(p2_ms)},
+        "gpu_launches": a.steps * (3 * R if R > 1 else 1),
+        "clocks": clocks,
+        "e2e": e2e,
+        "paper_context": {"seconds_n16384_fp32_tesla_c1060": PAPER_SECONDS_N16384,
+                          "ours_seconds": total_ms / a.steps / 1e3},
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a.dtype)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

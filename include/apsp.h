@@ -1,0 +1,174 @@
+/*
+ * apsp.h -- C ABI of libapsp, a GB300 (sm_103a) implementation of the blocked
+ * Floyd-Warshall all-pairs shortest-paths method of Lund & Smith, "A
+ * Multi-Stage CUDA Kernel for Floyd-Warshall".
+ *
+ * Problem (Sec. 3.1): a directed graph on n vertices is given by its n x n
+ * weight matrix W: w_ij is the weight of edge (v_i, v_j), "infinity" when the
+ * edge is absent, w_ii = 0, and no cycle has negative total weight.  The
+ * result d_ij (length of a shortest path from v_i to v_j) overwrites W in
+ * place, exactly as Fig. 1 leaves d^(n) in the incidence matrix.
+ *
+ * Method (Sec. 3.2, Fig. 2): the matrix is cut into s x s tiles; for every
+ * k-block b the "independent" diagonal tile is closed first (phase 1), then
+ * the "singly dependent" tiles of row b and column b (phase 2), then all other
+ * "doubly dependent" tiles, whose relaxations may run in any order (phase 3).
+ *
+ * Matrix layout for every entry point: row-major, leading dimension ld >= n
+ * (in elements); only the n x n leading block is read or written, columns
+ * n..ld-1 of each row are never touched.
+ *
+ * Value conventions
+ *   APSP_I32  int32_t.  Absent edge / unreachable pair = APSP_INF_I32 (2^29).
+ *             Inputs must satisfy w_ij <= 2^29 and (n-1)*(Wmax+|Wmin|) < 2^28,
+ *             where Wmax/Wmin range over the present edges; every output that
+ *             is >= 2^28 is written as 2^29.  The result is exact.
+ *   APSP_F32  float.  Absent edge / unreachable pair = +infinity.  Results
+ *             are computed with fp32 additions and exact minima; they are
+ *             bit-exact when all path sums are exactly representable.
+ *   APSP_I16  int16_t.  Absent edge / unreachable pair = APSP_INF_I16 (16383).
+ *             Requires non-negative weights with (n-1)*Wmax < 16383, so that no
+ *             sum of two entries leaves int16 and every unreachable pair ends
+ *             at exactly 16383; the result is exact.  Two adjacent columns are
+ *             relaxed per 32-bit lane (packed int16x2).
+ *
+ * Errors: every entry point returns an apsp_status.  Argument errors are
+ * reported synchronously and leave the matrix untouched.  Kernels are
+ * stream-ordered; an error that happens on the device is reported by the
+ * next call that synchronizes (APSP_ECUDA) or by apsp_device_error().
+ * A negative cycle in the input is not an error the library can see in
+ * general: the output is then unspecified (the paper excludes it).
+ *
+ * Threading: all entry points are reentrant for distinct matrices.
+ */
+#ifndef APSP_H
+#define APSP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define APSP_API __attribute__((visibility("default")))
+#else
+#define APSP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define APSP_INF_I32 (1 << 29)
+#define APSP_CLAMP_I32 (1 << 28)
+#define APSP_INF_I16 16383
+
+typedef enum apsp_dtype {
+    APSP_I32 = 0,
+    APSP_F32 = 1,
+    APSP_I16 = 2
+} apsp_dtype;
+
+typedef enum apsp_status {
+    APSP_OK = 0,
+    APSP_EINVAL = 1,      /* bad argument (null pointer, n < 0, ld < n, ...)  */
+    APSP_ENOMEM = 2,      /* an allocation failed                              */
+    APSP_EUNSUPPORTED = 3,/* valid request this build cannot serve             */
+    APSP_ECUDA = 4,       /* a CUDA runtime call failed                        */
+    APSP_ETIMEOUT = 5,    /* a bounded device-side wait gave up                */
+    APSP_EBUSY = 6,       /* resource in use (serving: no slot / memory)       */
+    APSP_EPENDING = 7,    /* serving: result not ready yet                     */
+    APSP_ENEGCYCLE = 8    /* negative cycle detected (only when asked)         */
+} apsp_status;
+
+/* Flags for apsp_options.flags. */
+#define APSP_FLAG_NO_GRAPH   0x1  /* launch the round loop directly, no CUDA graph        */
+#define APSP_FLAG_GENERIC    0x2  /* force the generic (non-TMA) phase-3 kernel           */
+#define APSP_FLAG_REVERSE_K  0x4  /* phase 3 visits the k-block in reverse order.  The
+                                     result must not change: the tasks of a doubly
+                                     dependent tile may run in any order (Sec. 3.2).     */
+#define APSP_FLAG_NEGCYCLE   0x8  /* after the solve, report APSP_ENEGCYCLE if some d_ii < 0
+                                     (synchronizes the stream)                           */
+
+typedef struct apsp_options {
+    int32_t kblock;          /* k-block depth s (64 or 128); 0 = chosen from n and dtype */
+    int32_t flags;           /* APSP_FLAG_* */
+    /* Optional tracing: an array of cudaEvent_t (cast to void*) of length
+       4 * rounds.  For round r the library records events[4r] before phase 1,
+       [4r+1] before phase 2, [4r+2] before phase 3 and [4r+3] after phase 3, on
+       the call's stream.  Tracing implies APSP_FLAG_NO_GRAPH.  NULL = off. */
+    void **events;
+    int64_t n_events;
+} apsp_options;
+
+/* Kernel configuration the library picks for (n, dtype); see apsp_options. */
+typedef struct apsp_config {
+    int32_t kblock;          /* s: tile side and k-block depth                     */
+    int32_t rounds;          /* ceil(n / s): stages of Fig. 2                       */
+    int32_t phase3_tma;      /* 1 if the TMA-staged phase-3 kernel is used          */
+    int32_t phase3_threads;  /* threads per phase-3 CTA                             */
+    int64_t phase3_relax_per_round; /* relaxations phase 3 performs in a full round */
+} apsp_config;
+
+/* Status name, e.g. "APSP_EINVAL".  Never NULL. */
+APSP_API const char *apsp_status_str(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+APSP_API int apsp_version(void);
+
+/*
+ * All-pairs shortest paths in place (Fig. 2, blocked Floyd-Warshall).
+ *   dist   device pointer to the n x n matrix (row-major, leading dim ld);
+ *          owned by the caller; overwritten with the distances.
+ *   n      vertices (0 is a no-op).
+ *   ld     leading dimension in elements, ld >= n.
+ *   dtype  APSP_I32 / APSP_F32 / APSP_I16.
+ *   stream cudaStream_t (cast to void*); NULL = legacy default stream.
+ * Stream-ordered: returns after the work is enqueued.  The fast phase-3 path
+ * needs dist 16-byte aligned and ld*sizeof(element) a multiple of 16; other
+ * layouts run a generic kernel (same results, slower).
+ * Returns APSP_EINVAL on a bad argument, APSP_ECUDA if a launch fails.
+ */
+APSP_API int apsp_fw(void *dist, int64_t n, int64_t ld, int dtype, void *stream);
+
+/* apsp_fw with options (NULL = defaults).  See apsp_options. */
+APSP_API int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt,
+               void *stream);
+
+/*
+ * apsp_fw on a matrix in HOST memory (pinned or pageable).  The library copies
+ * it to a device buffer it owns (kept for reuse, one per device), solves in
+ * place there and copies the result back.  Returns when the result is in
+ * host_dist (synchronizes the stream).
+ */
+APSP_API int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, void *stream);
+
+/* Fills *cfg with the configuration apsp_fw would use (no device work). */
+APSP_API int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_config *cfg);
+
+/*
+ * Device error word: bounded device-side waits that give up set it instead of
+ * hanging.  Returns 0 if clear, else the code of the first failure (and clears
+ * it when reset != 0).  Synchronizes the device.
+ */
+APSP_API int apsp_device_error(int reset);
+
+/*
+ * Roofline calibration: runs a dependent-chain-free stream of one min-plus
+ * instruction form on every SM and reports relaxations per second.
+ *   form   0 int32 add+min (DPX viaddmin), 1 fp32 add + min,
+ *          2 int16x2 packed DPX viaddmin (2 relaxations / instruction),
+ *          3 int32 separate add and min (no DPX),
+ *          4 fp32 packed f32x2 add + three-input min.
+ *   iters  inner iterations per thread (each does 64 relaxations per lane).
+ *   blocks, threads  launch shape (blocks <= 0: 4 per SM).
+ *   sink   device buffer of blocks*threads int32/float (results written so the
+ *          work is not eliminated).
+ *   relax_per_s  out: measured relaxations per second (host pointer).
+ * Synchronizes the stream.
+ */
+APSP_API int apsp_ubench_minplus(int form, int64_t iters, int blocks, int threads, void *sink,
+                        void *stream, double *relax_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APSP_H */

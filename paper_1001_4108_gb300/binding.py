@@ -1,0 +1,162 @@
+"""ctypes binding of libapsp (include/apsp.h): argument marshalling only.
+
+Every computation happens in the CUDA library.  ``lib()`` loads the in-tree
+``_lib/libapsp.so`` and raises if it is missing -- there is no fallback.
+Torch tensors are accepted for convenience: their data pointer, row stride
+and current CUDA stream are passed through unchanged.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libapsp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "apsp.h")
+
+APSP_I32, APSP_F32, APSP_I16 = 0, 1, 2
+APSP_OK, APSP_EINVAL, APSP_ENOMEM, APSP_EUNSUPPORTED, APSP_ECUDA = 0, 1, 2, 3, 4
+APSP_ETIMEOUT, APSP_EBUSY, APSP_EPENDING, APSP_ENEGCYCLE = 5, 6, 7, 8
+FLAG_NO_GRAPH, FLAG_GENERIC, FLAG_REVERSE_K, FLAG_NEGCYCLE = 0x1, 0x2, 0x4, 0x8
+INF_I32 = 1 << 29
+INF_I16 = 16383
+
+# Every symbol include/apsp.h declares (checked by the tests).
+EXPORTS = ["apsp_status_str", "apsp_version", "apsp_fw", "apsp_fw_ex", "apsp_fw_host",
+           "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("kblock", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("events", ctypes.POINTER(ctypes.c_void_p)), ("n_events", ctypes.c_int64)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("kblock", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("phase3_tma", ctypes.c_int32), ("phase3_threads", ctypes.c_int32),
+                ("phase3_relax_per_round", ctypes.c_int64)]
+
+
+class ApspError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libapsp.so (built by ``paper_1001_4108_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libapsp.so not built ({LIB_PATH}); run "
+                                   "`python -m paper_1001_4108_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            L.apsp_status_str.argtypes = [i32]
+            L.apsp_status_str.restype = ctypes.c_char_p
+            L.apsp_version.restype = i32
+            L.apsp_fw.argtypes = [vp, i64, i64, i32, vp]
+            L.apsp_fw_ex.argtypes = [vp, i64, i64, i32, ctypes.POINTER(Options), vp]
+            L.apsp_fw_host.argtypes = [vp, i64, i64, i32, vp]
+            L.apsp_query_config.argtypes = [i64, i32, ctypes.c_int32, ctypes.POINTER(Config)]
+            L.apsp_device_error.argtypes = [i32]
+            L.apsp_ubench_minplus.argtypes = [i32, i64, i32, i32, vp, vp, ctypes.POINTER(ctypes.c_double)]
+            for name in EXPORTS:
+                getattr(L, name).restype = getattr(L, name).restype or i32
+            L.apsp_status_str.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return lib().apsp_status_str(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != APSP_OK:
+        raise ApspError(status, what)
+
+
+def dtype_code(t) -> int:
+    """Map a torch/numpy dtype (or its name) to apsp_dtype."""
+    name = str(t).split(".")[-1]
+    return {"int32": APSP_I32, "float32": APSP_F32, "int16": APSP_I16}[name]
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _matrix_args(d, n):
+    """(ptr, n, ld, dtype) of a 2-D CUDA tensor whose leading n x n block is
+    the matrix (row stride = ld, unit column stride)."""
+    assert d.dim() == 2 and d.stride(1) == 1, "row-major matrix with unit column stride expected"
+    n = d.shape[0] if n is None else n
+    assert d.shape[0] >= n and d.shape[1] >= n
+    return d.data_ptr(), n, d.stride(0), dtype_code(d.dtype)
+
+
+def apsp_fw(d, n: int | None = None, *, kblock: int = 0, flags: int = 0, events=None, stream=None):
+    """In-place all-pairs shortest paths on a CUDA tensor (int32/float32/int16)."""
+    ptr, n, ld, dt = _matrix_args(d, n)
+    s = _stream_handle(stream)
+    if kblock == 0 and flags == 0 and events is None:
+        _check(lib().apsp_fw(ptr, n, ld, dt, s), "apsp_fw")
+        return d
+    opt = Options(kblock, flags, None, 0)
+    if events is not None:
+        arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+        opt.events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
+        opt.n_events = len(events)
+    _check(lib().apsp_fw_ex(ptr, n, ld, dt, ctypes.byref(opt), s), "apsp_fw_ex")
+    return d
+
+
+def apsp_fw_raw(ptr: int, n: int, ld: int, dtype: int, stream: int | None, opt: Options | None = None) -> int:
+    """Direct call returning the status code (used by argument-check tests)."""
+    if opt is None:
+        return lib().apsp_fw(ptr, n, ld, dtype, stream)
+    return lib().apsp_fw_ex(ptr, n, ld, dtype, ctypes.byref(opt), stream)
+
+
+def apsp_fw_host(a, stream=None):
+    """All-pairs shortest paths on a host (CPU) numpy array or torch tensor,
+    in place, through the library's host entry point (H2D, solve, D2H)."""
+    import numpy as np
+    if isinstance(a, np.ndarray):
+        assert a.ndim == 2 and a.strides[1] == a.itemsize
+        n, ld, dt, ptr = a.shape[0], a.strides[0] // a.itemsize, dtype_code(a.dtype), a.ctypes.data
+    else:
+        assert not a.is_cuda and a.stride(1) == 1
+        n, ld, dt, ptr = a.shape[0], a.stride(0), dtype_code(a.dtype), a.data_ptr()
+    _check(lib().apsp_fw_host(ptr, n, ld, dt, _stream_handle(stream)), "apsp_fw_host")
+    return a
+
+
+def query_config(n: int, dtype, kblock: int = 0) -> Config:
+    cfg = Config()
+    dt = dtype if isinstance(dtype, int) else dtype_code(dtype)
+    _check(lib().apsp_query_config(n, dt, kblock, ctypes.byref(cfg)), "apsp_query_config")
+    return cfg
+
+
+def device_error(reset: bool = True) -> int:
+    return lib().apsp_device_error(1 if reset else 0)
+
+
+def ubench(form: int, iters: int, sink, blocks: int = 0, threads: int = 256, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    _check(lib().apsp_ubench_minplus(form, iters, blocks, threads, sink.data_ptr(),
+                                     _stream_handle(stream), ctypes.byref(out)), "apsp_ubench_minplus")
+    return out.value

@@ -1,0 +1,284 @@
+// C ABI of libapsp (declared in include/apsp.h): argument checks, choice of
+// the tile side, CUDA-graph replay of the stage loop, the host-buffer entry
+// point and the device error word.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/apsp.h"
+#include "apsp_internal.h"
+
+// Device error word: bounded waits that give up record a code here.
+static __device__ int g_apsp_err;
+// Set by the negative-cycle check.
+static __device__ int g_apsp_negcycle;
+
+namespace apsp {
+
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+namespace {
+
+constexpr int kMaxDev = 64;
+
+std::mutex g_mu;
+int *g_err_ptr[kMaxDev];
+int *g_neg_ptr[kMaxDev];
+
+int elem_size(int dtype) { return dtype == APSP_I16 ? 2 : 4; }
+
+// Device addresses of the error words for the current device (looked up once
+// per device with that device current).
+int device_words(int **err, int **neg) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return APSP_ECUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_err_ptr[dev]) {
+    void *pe = nullptr, *pn = nullptr;
+    if (cudaGetSymbolAddress(&pe, g_apsp_err) != cudaSuccess) return APSP_ECUDA;
+    if (cudaGetSymbolAddress(&pn, g_apsp_negcycle) != cudaSuccess) return APSP_ECUDA;
+    g_err_ptr[dev] = static_cast<int *>(pe);
+    g_neg_ptr[dev] = static_cast<int *>(pn);
+  }
+  *err = g_err_ptr[dev];
+  if (neg) *neg = g_neg_ptr[dev];
+  return APSP_OK;
+}
+
+// Tile side s: 64 keeps enough doubly dependent tiles in flight for small n,
+// 128 halves the HBM traffic per relaxation (2 * elem / s bytes) for large n.
+int choose_kblock(int64_t n, int dtype, int32_t requested) {
+  if (requested == 64 || requested == 128) return requested;
+  (void)dtype;
+  return n < 4096 ? 64 : 128;
+}
+
+int check_args(const void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt) {
+  if (dtype != APSP_I32 && dtype != APSP_F32 && dtype != APSP_I16) return APSP_EINVAL;
+  if (n < 0 || ld < n || ld < 0) return APSP_EINVAL;
+  if (n > (int64_t)1 << 20) return APSP_EUNSUPPORTED;  // grid and int index limits
+  if (n > 0 && !dist) return APSP_EINVAL;
+  if (opt) {
+    if (opt->kblock != 0 && opt->kblock != 64 && opt->kblock != 128) return APSP_EINVAL;
+    if (opt->events && opt->n_events < 0) return APSP_EINVAL;
+  }
+  return APSP_OK;
+}
+
+int run_dtype(const RunArgs &a, int dtype) {
+  switch (dtype) {
+    case APSP_I32: return run_i32(a);
+    case APSP_F32: return run_f32(a);
+    case APSP_I16: return run_i16(a);
+  }
+  return APSP_EINVAL;
+}
+
+// ---------------------------------------------------------------- graphs
+// A solve is R * 3 launches.  Replaying them as one CUDA graph removes the
+// per-launch host cost, which dominates for small n.  A graph is captured the
+// second time the same (matrix, n, ld, dtype, s, flags) is solved, so one-off
+// calls do not pay the instantiation.
+struct GraphKey {
+  void *d;
+  int64_t n, ld;
+  int dtype, S, flags, dev;
+  bool operator==(const GraphKey &o) const {
+    return d == o.d && n == o.n && ld == o.ld && dtype == o.dtype && S == o.S && flags == o.flags && dev == o.dev;
+  }
+};
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+};
+constexpr size_t kMaxGraphs = 32;
+constexpr size_t kMaxSeen = 64;
+std::vector<GraphEntry> g_graphs;
+std::vector<GraphKey> g_seen;
+cudaStream_t g_capture_stream[kMaxDev];
+
+int launch_with_graph(const RunArgs &a, int dtype, int dev) {
+  const GraphKey key{a.d, a.n, a.ld, dtype, a.S, a.flags, dev};
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto &g : g_graphs)
+    if (g.key == key) return cudaGraphLaunch(g.exec, a.stream) == cudaSuccess ? APSP_OK : APSP_ECUDA;
+  const bool seen = std::find(g_seen.begin(), g_seen.end(), key) != g_seen.end();
+  if (!seen) {
+    if (g_seen.size() >= kMaxSeen) g_seen.erase(g_seen.begin());
+    g_seen.push_back(key);
+    return run_dtype(a, dtype);
+  }
+  if (!g_capture_stream[dev] &&
+      cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking) != cudaSuccess)
+    return APSP_ECUDA;
+  RunArgs c = a;
+  c.stream = g_capture_stream[dev];
+  if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return APSP_ECUDA;
+  const int st = run_dtype(c, dtype);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c.stream, &graph);
+  if (st != APSP_OK || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return st != APSP_OK ? st : APSP_ECUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return APSP_ECUDA;
+  if (g_graphs.size() >= kMaxGraphs) {
+    cudaGraphExecDestroy(g_graphs.front().exec);
+    g_graphs.erase(g_graphs.begin());
+  }
+  g_graphs.push_back({key, exec});
+  return cudaGraphLaunch(exec, a.stream) == cudaSuccess ? APSP_OK : APSP_ECUDA;
+}
+
+template <typename T>
+__global__ void diag_negative(const T *d, int64_t n, int64_t ld, int *flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (d[i * ld + i] < (T)0) atomicExch(flag, 1);
+}
+
+int check_negcycle(void *dist, int64_t n, int64_t ld, int dtype, cudaStream_t st, int *neg) {
+  if (cudaMemsetAsync(neg, 0, sizeof(int), st) != cudaSuccess) return APSP_ECUDA;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  if (dtype == APSP_I32) diag_negative<int32_t><<<blocks, 256, 0, st>>>((const int32_t *)dist, n, ld, neg);
+  if (dtype == APSP_F32) diag_negative<float><<<blocks, 256, 0, st>>>((const float *)dist, n, ld, neg);
+  if (dtype == APSP_I16) diag_negative<int16_t><<<blocks, 256, 0, st>>>((const int16_t *)dist, n, ld, neg);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, neg, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return APSP_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return APSP_ECUDA;
+  return h ? APSP_ENEGCYCLE : APSP_OK;
+}
+
+// Device buffer of apsp_fw_host, one per device, grown on demand.
+struct HostStage {
+  std::mutex mu;
+  void *buf = nullptr;
+  size_t bytes = 0;
+};
+HostStage g_host_stage[kMaxDev];
+
+}  // namespace
+}  // namespace apsp
+
+using namespace apsp;
+
+extern "C" const char *apsp_status_str(int s) {
+  switch (s) {
+    case APSP_OK: return "APSP_OK";
+    case APSP_EINVAL: return "APSP_EINVAL";
+    case APSP_ENOMEM: return "APSP_ENOMEM";
+    case APSP_EUNSUPPORTED: return "APSP_EUNSUPPORTED";
+    case APSP_ECUDA: return "APSP_ECUDA";
+    case APSP_ETIMEOUT: return "APSP_ETIMEOUT";
+    case APSP_EBUSY: return "APSP_EBUSY";
+    case APSP_EPENDING: return "APSP_EPENDING";
+    case APSP_ENEGCYCLE: return "APSP_ENEGCYCLE";
+  }
+  return "APSP_UNKNOWN";
+}
+
+extern "C" int apsp_version(void) { return 100; }
+
+extern "C" int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_config *cfg) {
+  if (!cfg || n < 0 || (dtype != APSP_I32 && dtype != APSP_F32 && dtype != APSP_I16)) return APSP_EINVAL;
+  if (kblock != 0 && kblock != 64 && kblock != 128) return APSP_EINVAL;
+  const int S = choose_kblock(n, dtype, kblock);
+  cfg->kblock = S;
+  cfg->rounds = (int32_t)((n + S - 1) / S);
+  cfg->phase3_tma = dtype != APSP_I16 ? 1 : 0;
+  cfg->phase3_threads = cfg->phase3_tma ? (S / 8) * (S / 8) : 256;
+  const int64_t m = std::max<int64_t>(n - S, 0);
+  cfg->phase3_relax_per_round = m * m * S;
+  return APSP_OK;
+}
+
+extern "C" int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt, void *stream) {
+  int st = check_args(dist, n, ld, dtype, opt);
+  if (st != APSP_OK) return st;
+  if (n == 0) return APSP_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= kMaxDev) return APSP_ECUDA;
+  int *err = nullptr, *neg = nullptr;
+  st = device_words(&err, &neg);
+  if (st != APSP_OK) return st;
+
+  RunArgs a{};
+  a.d = dist;
+  a.n = n;
+  a.ld = ld;
+  a.S = choose_kblock(n, dtype, opt ? opt->kblock : 0);
+  a.flags = opt ? opt->flags : 0;
+  a.events = opt ? opt->events : nullptr;
+  a.n_events = opt ? opt->n_events : 0;
+  a.stream = static_cast<cudaStream_t>(stream);
+  a.err = err;
+  const size_t es = (size_t)elem_size(dtype);
+  a.tma_ok = dtype != APSP_I16 && (reinterpret_cast<uintptr_t>(dist) % 16 == 0) && ((size_t)ld * es) % 16 == 0;
+
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(a.stream, &cap) != cudaSuccess) return APSP_ECUDA;
+  const bool direct = (a.flags & APSP_FLAG_NO_GRAPH) || a.events || cap != cudaStreamCaptureStatusNone;
+  st = direct ? run_dtype(a, dtype) : launch_with_graph(a, dtype, dev);
+  if (st != APSP_OK) return st;
+  if (a.flags & APSP_FLAG_NEGCYCLE) return check_negcycle(dist, n, ld, dtype, a.stream, neg);
+  return APSP_OK;
+}
+
+extern "C" int apsp_fw(void *dist, int64_t n, int64_t ld, int dtype, void *stream) {
+  return apsp_fw_ex(dist, n, ld, dtype, nullptr, stream);
+}
+
+extern "C" int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, void *stream) {
+  int st = check_args(host_dist, n, ld, dtype, nullptr);
+  if (st != APSP_OK) return st;
+  if (n == 0) return APSP_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= kMaxDev) return APSP_ECUDA;
+  const size_t es = (size_t)elem_size(dtype);
+  const int64_t dld = (n + 7) / 8 * 8;  // 16-byte aligned device rows
+  const size_t bytes = (size_t)n * dld * es;
+  HostStage &hs = g_host_stage[dev];
+  std::lock_guard<std::mutex> lk(hs.mu);
+  if (hs.bytes < bytes) {
+    if (hs.buf) {
+      cudaDeviceSynchronize();
+      cudaFree(hs.buf);
+      hs.buf = nullptr;
+      hs.bytes = 0;
+    }
+    if (cudaMalloc(&hs.buf, bytes) != cudaSuccess) return APSP_ENOMEM;
+    hs.bytes = bytes;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpy2DAsync(hs.buf, dld * es, host_dist, ld * es, n * es, n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return APSP_ECUDA;
+  st = apsp_fw_ex(hs.buf, n, dld, dtype, nullptr, stream);
+  if (st != APSP_OK) return st;
+  if (cudaMemcpy2DAsync(host_dist, ld * es, hs.buf, dld * es, n * es, n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return APSP_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? APSP_OK : APSP_ECUDA;
+}
+
+extern "C" int apsp_device_error(int reset) {
+  int *err = nullptr;
+  if (device_words(&err, nullptr) != APSP_OK) return -1;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+  int h = 0;
+  if (cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  if (reset && h && cudaMemset(err, 0, sizeof(int)) != cudaSuccess) return -1;
+  return h;
+}

@@ -1,0 +1,133 @@
+// Shared device-side definitions of libapsp: value conventions, the
+// relaxation w_ij <- min(w_ij, w_ik + w_kj) of Fig. 1 for each element type,
+// and the inline-PTX helpers (mbarrier, TMA) of the staged phase-3 kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace apsp {
+
+// Error codes a kernel can leave in the device error word.
+enum DeviceError : int {
+  kDevOk = 0,
+  kDevTimeoutTma = 1,  // an mbarrier wait for a TMA copy gave up
+};
+
+// Longest a bounded device wait spins before giving up (nanoseconds).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// ---------------------------------------------------------------------------
+// Element types.  Each storage type T has a compute type C used in shared
+// memory and registers, the "infinity" of its input convention, the
+// relaxation, and the output finish (clamp) applied in the last stage.
+// ---------------------------------------------------------------------------
+template <typename T> struct Arith;
+
+// int32: infinity = 2^29.  All entries stay <= 2^29 (they only decrease), so
+// the sum of two entries is <= 2^30 and never overflows; any value >= 2^28 is
+// "no path" under the documented weight bound and is written back as 2^29.
+template <> struct Arith<int32_t> {
+  using C = int32_t;
+  static constexpr int32_t kInfHost = 1 << 29;
+  __device__ __forceinline__ static C inf() { return 1 << 29; }
+  __device__ __forceinline__ static C load(int32_t v) { return v; }
+  __device__ __forceinline__ static C relax(C acc, C a, C b) {
+    return __viaddmin_s32(a, b, acc);  // min(a + b, acc) as one DPX operation
+  }
+  __device__ __forceinline__ static int32_t finish(C v) { return v >= (1 << 28) ? (1 << 29) : v; }
+};
+
+// fp32: infinity = +inf, exact under + and min; a + b is rounded once, the
+// minimum is exact, so the result does not depend on the order of the k's.
+template <> struct Arith<float> {
+  using C = float;
+  __device__ __forceinline__ static C inf() { return __int_as_float(0x7f800000); }
+  __device__ __forceinline__ static C load(float v) { return v; }
+  __device__ __forceinline__ static C relax(C acc, C a, C b) { return fminf(acc, __fadd_rn(a, b)); }
+  __device__ __forceinline__ static float finish(C v) { return v; }
+};
+
+// int16 (scalar kernels): computed in int32, infinity = 16383.  With
+// non-negative weights and (n-1)*Wmax < 16383 entries stay in [0, 16383],
+// sums fit easily and unreachable pairs end at exactly 16383.
+template <> struct Arith<int16_t> {
+  using C = int32_t;
+  __device__ __forceinline__ static C inf() { return 16383; }
+  __device__ __forceinline__ static C load(int16_t v) { return (C)v; }
+  __device__ __forceinline__ static C relax(C acc, C a, C b) { return __viaddmin_s32(a, b, acc); }
+  __device__ __forceinline__ static int16_t finish(C v) { return (int16_t)v; }
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers (sm_90+ forms, valid on sm_103a).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the given phase of an mbarrier; gives up after kWaitLimitNs and
+// returns false instead of hanging.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// 2-D tiled TMA load global -> shared, completion counted on an mbarrier.
+// (x, y) = (column, row) of the box origin; x * sizeof(elem) % 16 == 0.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Index of a pivot-excluding tile: tiles b (the pivot block) is skipped.
+__device__ __forceinline__ int skip_pivot(int t, int b) { return t < b ? t : t + 1; }
+
+}  // namespace apsp

@@ -1,0 +1,34 @@
+// Host-side interface between the C-ABI translation unit (api.cu) and the
+// per-element-type translation units (fw_i32.cu, fw_f32.cu, fw_i16.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace apsp {
+
+struct RunArgs {
+  void *d;            // device matrix
+  int64_t n, ld;      // vertices, leading dimension (elements)
+  int S;              // tile side = k-block depth (64 or 128)
+  int flags;          // APSP_FLAG_*
+  void **events;      // optional per-phase events (4 per round) or nullptr
+  int64_t n_events;
+  cudaStream_t stream;
+  int *err;           // device error word
+  bool tma_ok;        // layout allows the TMA-staged phase 3
+};
+
+// Enqueue every stage of Fig. 2 for one matrix.  Returns an apsp_status.
+int run_i32(const RunArgs &a);
+int run_f32(const RunArgs &a);
+int run_i16(const RunArgs &a);
+
+// cuTensorMapEncodeTiled from the driver, resolved once (nullptr if absent).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn();
+
+}  // namespace apsp

@@ -1,0 +1,74 @@
+"""The C-ABI library loads and exports every symbol include/apsp.h declares;
+host-side argument checks (no GPU work is issued by any call here)."""
+import ctypes
+import re
+
+import pytest
+
+from paper_1001_4108_gb300 import binding, build
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return binding.lib()
+
+
+def _declared_functions():
+    text = open(binding.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*APSP_API\s+(?:const\s+)?\w+\s*\*?\s*(apsp_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_what_binding_lists():
+    assert _declared_functions() == sorted(binding.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_no_other_symbols_leak():
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    apsp_syms = sorted({l.split()[-1] for l in out.splitlines() if " T apsp_" in l})
+    assert apsp_syms == sorted(binding.EXPORTS)
+
+
+def test_status_strings(L):
+    assert binding.status_str(0) == "APSP_OK"
+    assert binding.status_str(8) == "APSP_ENEGCYCLE"
+    assert binding.status_str(99) == "APSP_UNKNOWN"
+    assert L.apsp_version() >= 100
+
+
+@pytest.mark.parametrize("ptr,n,ld,dt", [
+    (0x1000, -1, 4, binding.APSP_I32),      # negative n
+    (0x1000, 8, 7, binding.APSP_I32),       # ld < n
+    (0, 8, 8, binding.APSP_F32),            # null matrix
+    (0x1000, 8, 8, 7),                      # unknown dtype
+])
+def test_bad_arguments_rejected_synchronously(L, ptr, n, ld, dt):
+    assert binding.apsp_fw_raw(ptr, n, ld, dt, None) == binding.APSP_EINVAL
+
+
+def test_bad_kblock_rejected(L):
+    opt = binding.Options(96, 0, None, 0)
+    assert binding.apsp_fw_raw(0x1000, 8, 8, binding.APSP_I32, None, opt) == binding.APSP_EINVAL
+
+
+def test_empty_matrix_is_a_noop(L):
+    assert binding.apsp_fw_raw(0, 0, 0, binding.APSP_I32, None) == binding.APSP_OK
+
+
+def test_query_config(L):
+    c = binding.query_config(16384, binding.APSP_F32)
+    assert c.kblock == 128 and c.rounds == 128 and c.phase3_tma == 1 and c.phase3_threads == 256
+    assert c.phase3_relax_per_round == (16384 - 128) ** 2 * 128
+    c = binding.query_config(1000, binding.APSP_I32)
+    assert c.kblock == 64 and c.rounds == 16
+    c = binding.query_config(1000, binding.APSP_I16, 128)
+    assert c.kblock == 128 and c.rounds == 8 and c.phase3_tma == 0
+    cfg = binding.Config()
+    assert L.apsp_query_config(10, 1, 100, ctypes.byref(cfg)) == binding.APSP_EINVAL

@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+int32 / int16: bit-exact.  fp32: |d_gpu - d_64| <= 1e-5 * max(|d_64|, S_ij)
+where S_ij bounds the sum of |w| along a shortest path (for non-negative
+weights S_ij = d_64; for the reweighted graphs the sum of |w'| along the path
+is at most d_0 + 2 * max p, d_0 the distance before reweighting).  fp32 with
+integer-valued weights and path sums < 2^24 is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1001_4108_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+INF = inputs.INF_I32
+FP32_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    binding.lib()
+    yield
+    assert binding.device_error() == 0
+
+
+def gpu_solve(w: np.ndarray, n=None, **kw) -> np.ndarray:
+    t = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+    binding.apsp_fw(t, n, **kw)
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def assert_fp32_close(d_gpu, d64, scale=None):
+    d_gpu = d_gpu.astype(np.float64)
+    assert np.array_equal(np.isinf(d_gpu), np.isinf(d64))
+    fin = np.isfinite(d64)
+    s = np.abs(d64) if scale is None else np.maximum(np.abs(d64), scale)
+    err = np.abs(d_gpu[fin] - d64[fin])
+    bound = FP32_RTOL * s[fin]
+    worst = np.max(err - bound) if err.size else -1
+    assert worst <= 0, f"max excess {worst}"
+
+
+# ------------------------------------------------------------------ int32 ---
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_c1_int32_exact(seed):
+    w = inputs.c1(seed=seed)
+    np.testing.assert_array_equal(gpu_solve(w), oracle.fw_int32_conv(w))
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 63, 64, 65, 127, 128, 129, 200, 257, 1000])
+@pytest.mark.parametrize("kblock", [64, 128])
+def test_ragged_int32_negative_weights(n, kblock):
+    w = inputs.int_graph(n, 0.2, 0, 1000, seed=n, potential_max=50)
+    np.testing.assert_array_equal(gpu_solve(w, kblock=kblock), oracle.fw_int32_conv(w))
+
+
+@pytest.mark.parametrize("n,ld", [(100, 104), (300, 301), (129, 160), (513, 515)])
+def test_leading_dimension_and_poison(n, ld):
+    # ld*4 % 16 != 0 for odd ld: the generic phase-3 kernel runs
+    w = inputs.int_graph(n, 0.3, 1, 1000, seed=ld, ld=ld)
+    out = gpu_solve(w, n)
+    np.testing.assert_array_equal(out[:, :n], oracle.fw_int32_conv(np.ascontiguousarray(w[:, :n])))
+    assert (out[:, n:] == -7).all(), "padding columns beyond n were written"
+
+
+def test_int32_unreachable_and_clamp():
+    # two components, one of them with negative edges: unreachable pairs must
+    # come back as exactly 2^29 (clamped), reachable ones exact
+    n = 300
+    w = inputs.int_graph(n, 0.05, 0, 1000, seed=5, potential_max=200)
+    w[:150, 150:] = INF
+    d = gpu_solve(w)
+    np.testing.assert_array_equal(d, oracle.fw_int32_conv(w))
+    assert (d[:150, 150:] == INF).all()
+
+
+def test_generic_equals_tma_int32():
+    w = inputs.c1(seed=3)
+    a = gpu_solve(w)
+    b = gpu_solve(w, flags=binding.FLAG_GENERIC)
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("dt", ["i32", "f32"])
+def test_phase3_order_independence(dt):
+    # Sec. 3.2: the tasks of a doubly dependent block may run in any order.
+    # Reversing the k order inside phase 3 must give bit-identical results.
+    if dt == "i32":
+        w = inputs.int_graph(700, 0.2, 0, 1000, seed=9, potential_max=30)
+    else:
+        w = inputs.dense_f32(700, seed=9)
+    for kb in (64, 128):
+        a = gpu_solve(w, kblock=kb)
+        b = gpu_solve(w, kblock=kb, flags=binding.FLAG_REVERSE_K)
+        c = gpu_solve(w, kblock=kb, flags=binding.FLAG_REVERSE_K | binding.FLAG_GENERIC)
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_graph_replay_same_buffer():
+    w = inputs.c1(seed=4, n=520)
+    exp = oracle.fw_int32_conv(w)
+    src = torch.from_numpy(w).cuda()
+    t = torch.empty_like(src)
+    for _ in range(4):  # direct launch, capture, replay, replay
+        t.copy_(src)
+        binding.apsp_fw(t)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(t.cpu().numpy(), exp)
+
+
+def test_capture_into_user_graph():
+    w = inputs.c1(seed=6, n=300)
+    src = torch.from_numpy(w).cuda()
+    t = src.clone()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        binding.apsp_fw(t, stream=s)
+    t.copy_(src)
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
+
+
+def test_negative_cycle_flag():
+    w = np.array([[0, 1, INF], [-3, 0, 1], [INF, INF, 0]], np.int32)
+    t = torch.from_numpy(w).cuda()
+    st = binding.apsp_fw_raw(t.data_ptr(), 3, 3, binding.APSP_I32, torch.cuda.current_stream().cuda_stream,
+                             binding.Options(0, binding.FLAG_NEGCYCLE, None, 0))
+    assert st == binding.APSP_ENEGCYCLE
+    w2 = inputs.c1(seed=1, n=100)
+    t2 = torch.from_numpy(w2).cuda()
+    st = binding.apsp_fw_raw(t2.data_ptr(), 100, 100, binding.APSP_I32, torch.cuda.current_stream().cuda_stream,
+                             binding.Options(0, binding.FLAG_NEGCYCLE, None, 0))
+    assert st == binding.APSP_OK
+
+
+# ------------------------------------------------------------------- fp32 ---
+
+@pytest.mark.parametrize("n", [5, 64, 100, 129, 777])
+def test_fp32_integer_weights_bit_exact(n):
+    w = inputs.int_graph(n, 0.3, 1, 1000, seed=n)
+    wf = np.where(w == INF, np.inf, w).astype(np.float32)
+    d = gpu_solve(wf)
+    exp = oracle.fw_int32_conv(w).astype(np.float64)
+    exp[exp == INF] = np.inf
+    np.testing.assert_array_equal(d.astype(np.float64), exp)
+
+
+@pytest.mark.parametrize("n", [300, 2048])
+def test_c2_dense_fp32(n):
+    w = inputs.dense_f32(n, seed=n)
+    assert_fp32_close(gpu_solve(w), oracle.fw_f64(w))
+
+
+@pytest.mark.parametrize("n", [257, 1024])
+def test_c2_reweighted_fp32(n):
+    w, pot = inputs.dense_f32(n, seed=n + 1, reweighted=True)
+    d64 = oracle.fw_f64(w)
+    d0 = d64 - pot[:, None] + pot[None, :]
+    scale = np.abs(d0) + 2 * pot.max()
+    assert_fp32_close(gpu_solve(w), d64, scale)
+
+
+# ------------------------------------------------------------------ int16 ---
+
+@pytest.mark.parametrize("n", [1, 33, 130, 2048])
+def test_c3_int16_exact(n):
+    w32, w16 = inputs.c3(seed=n, n=n)
+    d16 = gpu_solve(w16)
+    d32 = gpu_solve(w32)
+    np.testing.assert_array_equal(d16, oracle.fw_int16_conv(w16))
+    np.testing.assert_array_equal(np.where(d16 == inputs.INF_I16, INF, d16.astype(np.int32)), d32)
+
+
+# --------------------------------------------------------------- host path ---
+
+def test_host_entry_point():
+    w = inputs.int_graph(333, 0.2, 1, 1000, seed=2, ld=340)
+    exp = oracle.fw_int32_conv(np.ascontiguousarray(w[:, :333]))
+    a = w.copy()
+    view = a[:, :333]
+    binding.lib().apsp_fw_host(view.ctypes.data, 333, 340, binding.APSP_I32,
+                               torch.cuda.current_stream().cuda_stream)
+    np.testing.assert_array_equal(a[:, :333], exp)
+    assert (a[:, 333:] == -7).all()
+    f = inputs.dense_f32(500, seed=3)
+    g = f.copy()
+    binding.apsp_fw_host(g)
+    assert_fp32_close(g, oracle.fw_f64(f))
+
+
+# ------------------------------------------------------- full size, sampled ---
+
+@pytest.mark.parametrize("dt", ["f32", "i32"])
+def test_full_size_16384_sampled(dt):
+    """n = 16384 in the bench's configuration: sampled rows against Dijkstra
+    (exact), sampled triangle-inequality triples and Bellman rows."""
+    n = 16384
+    if dt == "f32":
+        w = inputs.dense_f32(n, seed=0)
+    else:
+        w = inputs.int_graph(n, 0.3, 1, 1000, seed=0)
+    t = torch.from_numpy(w).cuda()
+    binding.apsp_fw(t)
+    torch.cuda.synchronize()
+    g = inputs.rng(77)
+    rows = g.choice(n, size=6, replace=False)
+    d_rows = t[torch.from_numpy(rows).cuda()].cpu().numpy()
+    if dt == "f32":
+        exact = oracle.dijkstra_rows_f32(w, rows)
+        assert_fp32_close(d_rows, exact)
+    else:
+        exact = oracle.dijkstra_rows_i32(w, rows)
+        np.testing.assert_array_equal(d_rows, exact)
+    # triangle inequality on 10^6 random triples (within fp32 rounding)
+    i = torch.from_numpy(g.integers(0, n, 1_000_000)).cuda()
+    j = torch.from_numpy(g.integers(0, n, 1_000_000)).cuda()
+    k = torch.from_numpy(g.integers(0, n, 1_000_000)).cuda()
+    dij = t[i, j].double().cpu().numpy()
+    dik = t[i, k].double().cpu().numpy()
+    dkj = t[k, j].double().cpu().numpy()
+    slack = 1e-5 * (np.abs(dik) + np.abs(dkj)) if dt == "f32" else 0
+    assert (dij <= dik + dkj + slack).all()
+    assert (t.diagonal() == 0).all().item()
