@@ -205,6 +205,9 @@ def run_ours(a):
 
     nev = 4 * R
     step_events = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(a.steps)]
+    for evs in step_events:  # torch creates the CUDA event on its first record
+        for e in evs:
+            e.record(stream)
 
     def step(events=None):
         work.copy_(pristine)

@@ -116,7 +116,10 @@ def apsp_fw(d, n: int | None = None, *, kblock: int = 0, flags: int = 0, events=
         return d
     opt = Options(kblock, flags, None, 0)
     if events is not None:
-        arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+        handles = [e.cuda_event for e in events]
+        if not all(handles):
+            raise ValueError("events must be created (recorded once) before they are passed in")
+        arr = (ctypes.c_void_p * len(events))(*handles)
         opt.events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
         opt.n_events = len(events)
     _check(lib().apsp_fw_ex(ptr, n, ld, dt, ctypes.byref(opt), s), "apsp_fw_ex")

@@ -230,3 +230,17 @@ def test_full_size_16384_sampled(dt):
     slack = 1e-5 * (np.abs(dik) + np.abs(dkj)) if dt == "f32" else 0
     assert (dij <= dik + dkj + slack).all()
     assert (t.diagonal() == 0).all().item()
+
+
+def test_traced_events_per_phase():
+    # the tracing option records 4 events per stage on the call's stream
+    w = inputs.dense_f32(400, seed=12)
+    t = torch.from_numpy(w).cuda()
+    cfg = binding.query_config(400, binding.APSP_F32)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(4 * cfg.rounds)]
+    for e in evs:
+        e.record()
+    binding.apsp_fw(t, events=evs)
+    torch.cuda.synchronize()
+    assert all(evs[i].elapsed_time(evs[i + 1]) >= 0 for i in range(len(evs) - 1))
+    assert_fp32_close(t.cpu().numpy(), oracle.fw_f64(w))
