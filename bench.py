@@ -279,11 +279,16 @@ def run_ours(a):
     peaks, peak_kind = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # min-plus ALU roofline: every SM issues 4 warp-instructions (128 lanes)
-    # per clock; one relaxation needs at least one instruction (DPX add-min
-    # for int32, half of a packed f32x2 add + half of a three-input min for
-    # fp32), so the ceiling is SMs x f_max x 128 relaxations per second.
-    peak = sms * sm_max * 1e6 * 128
+    # Min-plus ALU roofline.  The minimum runs on the ALU pipe: 16 lanes per
+    # SM sub-partition, 64 per SM per clock.  int32: one DPX add-min per
+    # relaxation -> 64 relaxations/clock/SM.  fp32: one three-input min folds
+    # two candidates (after one packed f32x2 add) -> 128 relaxations/clock/SM.
+    lanes = 128 if a.dtype == "f32" else 64
+    peak = sms * sm_max * 1e6 * lanes
+    # the same instruction form in isolation (phase-3 inner loop on shared-
+    # memory operands, every SM): the sustained ceiling of the form
+    sink = torch.empty(sms * 2 * 256, dtype=torch.int32, device="cuda")
+    form_ceiling = binding.ubench(4 if a.dtype == "f32" else 0, 2000, sink)
     p3_relax = float(cfg.phase3_relax_per_round)
     p3_mean_s = statistics.mean(p3_ms) * 1e-3 if p3_ms else float("nan")
     achieved = p3_relax / p3_mean_s
@@ -297,9 +302,13 @@ def run_ours(a):
         "config": {"workload": _workload_name(a.dtype, n), "n": n, "kblock": cfg.kblock, "rounds": R,
                    "l2": "inputs larger than L2 (matrix %.2f GiB)" % (n * n * es / 2 ** 30),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "alu", "kernel": "fw_phase3_tma", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "alu",
+                     "kernel": "fw_phase3_f32x2" if a.dtype == "f32" else "fw_tile_tma<int,128,0>",
+                     "achieved": achieved, "peak": peak,
                      "unit": "relaxations/s", "frac": achieved / peak,
-                     "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz ({peak_kind} max clock) x 128 lanes / 1 instr",
+                     "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz ({peak_kind} max clock) x {lanes} relaxations "
+                                   "per clock per SM (64 ALU-pipe lanes; fp32: 2 per three-input min)",
+                     "form_ceiling": form_ceiling, "frac_of_form_ceiling": achieved / form_ceiling,
                      "traffic": None,
                      "algorithmic_hbm_GBps": hbm_bytes / p3_mean_s / 1e9,
                      "hbm_peak_GBps": peaks.get("hbm_gbs"),

@@ -86,6 +86,8 @@ typedef enum apsp_status {
                                      dependent tile may run in any order (Sec. 3.2).     */
 #define APSP_FLAG_NEGCYCLE   0x8  /* after the solve, report APSP_ENEGCYCLE if some d_ii < 0
                                      (synchronizes the stream)                           */
+#define APSP_FLAG_NO_WORKSPACE 0x10 /* use only kernels that need no device workspace
+                                     (same results, slower for fp32)                     */
 
 typedef struct apsp_options {
     int32_t kblock;          /* k-block depth s (64 or 128); 0 = chosen from n and dtype */
@@ -96,6 +98,13 @@ typedef struct apsp_options {
        the call's stream.  Tracing implies APSP_FLAG_NO_GRAPH.  NULL = off. */
     void **events;
     int64_t n_events;
+    /* Optional device workspace of at least apsp_workspace_bytes(n, dtype,
+       kblock) bytes, 256-byte aligned, owned by the caller and used only
+       between the enqueue and the completion of this call's work on its stream.
+       NULL = the library uses a buffer of its own, one per (device, stream),
+       allocated on first use (not while the stream is being captured). */
+    void *workspace;
+    int64_t workspace_bytes;
 } apsp_options;
 
 /* Kernel configuration the library picks for (n, dtype); see apsp_options. */
@@ -140,6 +149,15 @@ APSP_API int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const apsp
  */
 APSP_API int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, void *stream);
 
+/*
+ * Device workspace (bytes) a solve of this size uses; 0 if none.  fp32 solves
+ * keep a k-pair-interleaved copy of the current pivot row panel there
+ * (s * ceil(n/s) * s * 4 bytes, e.g. 8 MiB at n = 16384, s = 128), written by
+ * phase 2 and read by phase 3.  Without a workspace the same results come
+ * from a slower phase-3 kernel.
+ */
+APSP_API int64_t apsp_workspace_bytes(int64_t n, int dtype, int32_t kblock);
+
 /* Fills *cfg with the configuration apsp_fw would use (no device work). */
 APSP_API int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_config *cfg);
 
@@ -151,16 +169,20 @@ APSP_API int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_config
 APSP_API int apsp_device_error(int reset);
 
 /*
- * Roofline calibration: runs a dependent-chain-free stream of one min-plus
- * instruction form on every SM and reports relaxations per second.
- *   form   0 int32 add+min (DPX viaddmin), 1 fp32 add + min,
- *          2 int16x2 packed DPX viaddmin (2 relaxations / instruction),
- *          3 int32 separate add and min (no DPX),
- *          4 fp32 packed f32x2 add + three-input min.
- *   iters  inner iterations per thread (each does 64 relaxations per lane).
- *   blocks, threads  launch shape (blocks <= 0: 4 per SM).
- *   sink   device buffer of blocks*threads int32/float (results written so the
- *          work is not eliminated).
+ * Roofline calibration: runs the phase-3 inner loop of one instruction form on
+ * every SM, with operands loaded from shared memory at every k step as in the
+ * kernels (256 threads, 8 x 8 register micro-tile, a 32-k slice swept `iters`
+ * times), and reports relaxations per second.
+ *   form   0 int32 DPX add-min (one relaxation per instruction),
+ *          1 fp32 add then min,
+ *          2 int16x2 DPX add-min (two relaxations per instruction),
+ *          3 int32 add then min as separate instructions,
+ *          4 fp32 packed add.f32x2 + three-input min (two k's per pair),
+ *          5 int32 two adds + three-input DPX min (two k's).
+ *   iters  sweeps of the slice.
+ *   blocks blocks to launch (<= 0: 2 per SM); threads must be 256.
+ *   sink   device buffer of blocks*256 4-byte words (results are written so
+ *          the work is not eliminated).
  *   relax_per_s  out: measured relaxations per second (host pointer).
  * Synchronizes the stream.
  */

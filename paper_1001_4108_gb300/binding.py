@@ -18,18 +18,19 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "apsp.h")
 APSP_I32, APSP_F32, APSP_I16 = 0, 1, 2
 APSP_OK, APSP_EINVAL, APSP_ENOMEM, APSP_EUNSUPPORTED, APSP_ECUDA = 0, 1, 2, 3, 4
 APSP_ETIMEOUT, APSP_EBUSY, APSP_EPENDING, APSP_ENEGCYCLE = 5, 6, 7, 8
-FLAG_NO_GRAPH, FLAG_GENERIC, FLAG_REVERSE_K, FLAG_NEGCYCLE = 0x1, 0x2, 0x4, 0x8
+FLAG_NO_GRAPH, FLAG_GENERIC, FLAG_REVERSE_K, FLAG_NEGCYCLE, FLAG_NO_WORKSPACE = 0x1, 0x2, 0x4, 0x8, 0x10
 INF_I32 = 1 << 29
 INF_I16 = 16383
 
 # Every symbol include/apsp.h declares (checked by the tests).
 EXPORTS = ["apsp_status_str", "apsp_version", "apsp_fw", "apsp_fw_ex", "apsp_fw_host",
-           "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus"]
+           "apsp_workspace_bytes", "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus"]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("kblock", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("events", ctypes.POINTER(ctypes.c_void_p)), ("n_events", ctypes.c_int64)]
+                ("events", ctypes.POINTER(ctypes.c_void_p)), ("n_events", ctypes.c_int64),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_int64)]
 
 
 class Config(ctypes.Structure):
@@ -46,6 +47,14 @@ class ApspError(RuntimeError):
 
 _lock = threading.Lock()
 _lib = None
+_path = LIB_PATH
+
+
+def use_library(path: str):
+    """Select another build of libapsp.so (a tuning variant) before first use."""
+    global _path
+    assert _lib is None, "library already loaded"
+    _path = path
 
 
 def lib() -> ctypes.CDLL:
@@ -53,10 +62,10 @@ def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"libapsp.so not built ({LIB_PATH}); run "
+            if not os.path.exists(_path):
+                raise RuntimeError(f"libapsp.so not built ({_path}); run "
                                    "`python -m paper_1001_4108_gb300.build`")
-            L = ctypes.CDLL(LIB_PATH)
+            L = ctypes.CDLL(_path)
             vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
             L.apsp_status_str.argtypes = [i32]
             L.apsp_status_str.restype = ctypes.c_char_p
@@ -65,6 +74,8 @@ def lib() -> ctypes.CDLL:
             L.apsp_fw_ex.argtypes = [vp, i64, i64, i32, ctypes.POINTER(Options), vp]
             L.apsp_fw_host.argtypes = [vp, i64, i64, i32, vp]
             L.apsp_query_config.argtypes = [i64, i32, ctypes.c_int32, ctypes.POINTER(Config)]
+            L.apsp_workspace_bytes.argtypes = [i64, i32, ctypes.c_int32]
+            L.apsp_workspace_bytes.restype = i64
             L.apsp_device_error.argtypes = [i32]
             L.apsp_ubench_minplus.argtypes = [i32, i64, i32, i32, vp, vp, ctypes.POINTER(ctypes.c_double)]
             for name in EXPORTS:
@@ -107,14 +118,19 @@ def _matrix_args(d, n):
     return d.data_ptr(), n, d.stride(0), dtype_code(d.dtype)
 
 
-def apsp_fw(d, n: int | None = None, *, kblock: int = 0, flags: int = 0, events=None, stream=None):
-    """In-place all-pairs shortest paths on a CUDA tensor (int32/float32/int16)."""
+def apsp_fw(d, n: int | None = None, *, kblock: int = 0, flags: int = 0, events=None, stream=None,
+            workspace=None):
+    """In-place all-pairs shortest paths on a CUDA tensor (int32/float32/int16).
+    ``workspace``: optional CUDA tensor used as the device workspace."""
     ptr, n, ld, dt = _matrix_args(d, n)
     s = _stream_handle(stream)
-    if kblock == 0 and flags == 0 and events is None:
+    if kblock == 0 and flags == 0 and events is None and workspace is None:
         _check(lib().apsp_fw(ptr, n, ld, dt, s), "apsp_fw")
         return d
-    opt = Options(kblock, flags, None, 0)
+    opt = Options(kblock, flags, None, 0, None, 0)
+    if workspace is not None:
+        opt.workspace = workspace.data_ptr()
+        opt.workspace_bytes = workspace.numel() * workspace.element_size()
     if events is not None:
         handles = [e.cuda_event for e in events]
         if not all(handles):
@@ -145,6 +161,11 @@ def apsp_fw_host(a, stream=None):
         n, ld, dt, ptr = a.shape[0], a.stride(0), dtype_code(a.dtype), a.data_ptr()
     _check(lib().apsp_fw_host(ptr, n, ld, dt, _stream_handle(stream)), "apsp_fw_host")
     return a
+
+
+def workspace_bytes(n: int, dtype, kblock: int = 0) -> int:
+    dt = dtype if isinstance(dtype, int) else dtype_code(dtype)
+    return int(lib().apsp_workspace_bytes(n, dt, kblock))
 
 
 def query_config(n: int, dtype, kblock: int = 0) -> Config:

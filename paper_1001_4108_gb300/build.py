@@ -49,15 +49,22 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False,
+          defines=(), out_dir: str | None = None) -> str:
+    """Compile and link libapsp.so; returns its path.  ``defines`` (e.g.
+    ["APSP_P3_MINB=1"]) and ``out_dir`` build a tuning variant elsewhere."""
     nvcc = _nvcc()
-    os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
+    out_dir_ = OUT_DIR if out_dir is None else out_dir
+    obj_dir = OBJ_DIR if out_dir is None else os.path.join(out_dir, "_build")
+    lib = os.path.join(out_dir_, "libapsp.so")
+    os.makedirs(out_dir_, exist_ok=True)
+    os.makedirs(obj_dir, exist_ok=True)
+    dflags = [f"-D{d}" for d in defines]
     jobs = []
     for src in SOURCES:
-        obj = os.path.join(OBJ_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
         if force or _stale(obj, list(_deps(src))):
-            cmd = [nvcc] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_verbose else []) + \
+            cmd = [nvcc] + NVCC_FLAGS + dflags + (["-Xptxas", "-v"] if ptxas_verbose else []) + \
                   ["-c", os.path.join(CSRC, src), "-o", obj]
             jobs.append((src, cmd))
     if jobs:
@@ -72,15 +79,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
                     failed.append(futs[f])
             if failed:
                 raise RuntimeError(f"nvcc failed for {failed}")
-    objs = [os.path.join(OBJ_DIR, s.replace(".cu", ".o")) for s in SOURCES]
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [os.path.join(obj_dir, s.replace(".cu", ".o")) for s in SOURCES]
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -95,8 +95,11 @@ struct GraphKey {
   void *d;
   int64_t n, ld;
   int dtype, S, flags, dev;
+  cudaStream_t stream;
+  void *ws;
   bool operator==(const GraphKey &o) const {
-    return d == o.d && n == o.n && ld == o.ld && dtype == o.dtype && S == o.S && flags == o.flags && dev == o.dev;
+    return d == o.d && n == o.n && ld == o.ld && dtype == o.dtype && S == o.S && flags == o.flags &&
+           dev == o.dev && stream == o.stream && ws == o.ws;
   }
 };
 struct GraphEntry {
@@ -110,7 +113,7 @@ std::vector<GraphKey> g_seen;
 cudaStream_t g_capture_stream[kMaxDev];
 
 int launch_with_graph(const RunArgs &a, int dtype, int dev) {
-  const GraphKey key{a.d, a.n, a.ld, dtype, a.S, a.flags, dev};
+  const GraphKey key{a.d, a.n, a.ld, dtype, a.S, a.flags, dev, a.stream, a.ws};
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto &g : g_graphs)
     if (g.key == key) return cudaGraphLaunch(g.exec, a.stream) == cudaSuccess ? APSP_OK : APSP_ECUDA;
@@ -163,6 +166,71 @@ int check_negcycle(void *dist, int64_t n, int64_t ld, int dtype, cudaStream_t st
   return h ? APSP_ENEGCYCLE : APSP_OK;
 }
 
+// Library-owned workspaces, one per (device, stream): work on one stream is
+// ordered, so a stream's solves can share one buffer.  Allocated outside of
+// stream capture only; grown on demand.
+struct WsEntry {
+  int dev;
+  cudaStream_t stream;
+  void *p;
+  size_t bytes;
+};
+constexpr size_t kMaxWs = 16;
+std::vector<WsEntry> g_ws;
+
+// Graphs captured with a workspace bake its address in: drop them before the
+// buffer is freed.  Caller holds g_mu.
+void forget_graphs_using(void *ws) {
+  for (size_t i = 0; i < g_graphs.size();) {
+    if (g_graphs[i].key.ws == ws) {
+      cudaGraphExecDestroy(g_graphs[i].exec);
+      g_graphs.erase(g_graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+  g_seen.erase(std::remove_if(g_seen.begin(), g_seen.end(), [&](const GraphKey &k) { return k.ws == ws; }),
+               g_seen.end());
+}
+
+void *library_workspace(int dev, cudaStream_t stream, size_t bytes, bool capturing, size_t *got) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto &e : g_ws)
+    if (e.dev == dev && e.stream == stream) {
+      if (e.bytes >= bytes) {
+        *got = e.bytes;
+        return e.p;
+      }
+      if (capturing) return nullptr;
+      cudaDeviceSynchronize();
+      forget_graphs_using(e.p);
+      cudaFree(e.p);
+      e.p = nullptr;
+      e.bytes = 0;
+      if (cudaMalloc(&e.p, bytes) != cudaSuccess) return nullptr;
+      e.bytes = bytes;
+      *got = bytes;
+      return e.p;
+    }
+  if (capturing) return nullptr;
+  if (g_ws.size() >= kMaxWs) {
+    cudaDeviceSynchronize();
+    forget_graphs_using(g_ws.front().p);
+    cudaFree(g_ws.front().p);
+    g_ws.erase(g_ws.begin());
+  }
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  g_ws.push_back({dev, stream, p, bytes});
+  *got = bytes;
+  return p;
+}
+
+size_t workspace_bytes_for(int64_t n, int dtype, int S) {
+  if (dtype != APSP_F32 || n <= S) return 0;
+  return interleaved_panel_bytes(n, S);
+}
+
 // Device buffer of apsp_fw_host, one per device, grown on demand.
 struct HostStage {
   std::mutex mu;
@@ -192,6 +260,11 @@ extern "C" const char *apsp_status_str(int s) {
 }
 
 extern "C" int apsp_version(void) { return 100; }
+
+extern "C" int64_t apsp_workspace_bytes(int64_t n, int dtype, int32_t kblock) {
+  if (n < 0 || (dtype != APSP_I32 && dtype != APSP_F32 && dtype != APSP_I16)) return 0;
+  return (int64_t)workspace_bytes_for(n, dtype, choose_kblock(n, dtype, kblock));
+}
 
 extern "C" int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_config *cfg) {
   if (!cfg || n < 0 || (dtype != APSP_I32 && dtype != APSP_F32 && dtype != APSP_I16)) return APSP_EINVAL;
@@ -231,6 +304,17 @@ extern "C" int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const ap
 
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(a.stream, &cap) != cudaSuccess) return APSP_ECUDA;
+  const size_t need = (a.flags & APSP_FLAG_NO_WORKSPACE) ? 0 : workspace_bytes_for(n, dtype, a.S);
+  if (need) {
+    if (opt && opt->workspace) {
+      if (opt->workspace_bytes < (int64_t)need || reinterpret_cast<uintptr_t>(opt->workspace) % 256) return APSP_EINVAL;
+      a.ws = opt->workspace;
+      a.ws_bytes = (size_t)opt->workspace_bytes;
+    } else {
+      a.ws = library_workspace(dev, a.stream, need, cap != cudaStreamCaptureStatusNone, &a.ws_bytes);
+      if (!a.ws) a.ws_bytes = 0;  // the kernels fall back to the form that needs none
+    }
+  }
   const bool direct = (a.flags & APSP_FLAG_NO_GRAPH) || a.events || cap != cudaStreamCaptureStatusNone;
   st = direct ? run_dtype(a, dtype) : launch_with_graph(a, dtype, dev);
   if (st != APSP_OK) return st;

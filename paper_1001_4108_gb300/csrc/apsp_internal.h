@@ -18,7 +18,15 @@ struct RunArgs {
   cudaStream_t stream;
   int *err;           // device error word
   bool tma_ok;        // layout allows the TMA-staged phase 3
+  void *ws;           // device workspace (256-byte aligned) or nullptr
+  size_t ws_bytes;
 };
+
+// Workspace bytes of the packed fp32 phase 3 (interleaved row panel).
+inline size_t interleaved_panel_bytes(int64_t n, int S) {
+  const int64_t np = (n + S - 1) / S * S;
+  return (size_t)S * (size_t)np * sizeof(float);
+}
 
 // Enqueue every stage of Fig. 2 for one matrix.  Returns an apsp_status.
 int run_i32(const RunArgs &a);

@@ -6,6 +6,8 @@
 #include "apsp_internal.h"
 #include "fw_kernels.cuh"
 
+#include <type_traits>
+
 namespace apsp {
 
 template <typename T> struct TmaType;
@@ -33,21 +35,33 @@ static bool make_panel_maps(T *d, int64_t n, int64_t ld, CUtensorMap *mA, CUtens
   return true;
 }
 
+// Tensor map of the k-pair interleaved row panel (S/2 rows x 2 n_p floats).
+template <int S>
+static bool make_interleaved_map(float *bp, int64_t np, CUtensorMap *m) {
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * np), (cuuint64_t)(S / 2)};
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * np) * sizeof(float)};
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * S), (cuuint32_t)(P3Tma<S>::KS / 2)};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, bp, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename T, int S>
 struct Kernels {
-  static constexpr int NT12 = S == 64 ? 256 : 1024;
+  static constexpr int NT1 = (S / 4) * (S / 4);
+  static constexpr int NT2 = S == 64 ? 256 : 1024;
   using C = typename Arith<T>::C;
-  static constexpr size_t SM1 = (size_t)S * S * sizeof(C);
-  static constexpr size_t SM2 = 2 * SM1;
+  static constexpr size_t SM2 = 2 * (size_t)S * S * sizeof(C);
   static constexpr size_t SM3G = ((size_t)S * (S + 1) + (size_t)S * S) * sizeof(C);
 
   // Raises the dynamic shared-memory limit of each kernel once per process
   // and device (the attribute is per device).
   static cudaError_t setup() {
     cudaError_t e;
-    e = cudaFuncSetAttribute(fw_phase1<T, S, NT12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fw_phase2<T, S, NT12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);
+    e = cudaFuncSetAttribute(fw_phase2<T, S, NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fw_phase3_generic<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM3G);
     return e;
@@ -63,9 +77,20 @@ static int run_rounds(const RunArgs &a) {
   if (!(setup_done_mask & (1 << (dev & 31)))) {
     if (K::setup() != cudaSuccess) return APSP_ECUDA;
     if constexpr (HAS_TMA) {
-      if (cudaFuncSetAttribute(fw_phase3_tma<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if (cudaFuncSetAttribute(fw_tile_tma<T, S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               P3Tma<S>::SMEM) != cudaSuccess ||
+          cudaFuncSetAttribute(fw_tile_tma<T, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                P3Tma<S>::SMEM) != cudaSuccess)
         return APSP_ECUDA;
+      if constexpr (std::is_same<T, float>::value) {
+        const int sm = P3Tma<S>::SMEM;
+        const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (cudaFuncSetAttribute(fw_phase3_f32x2<S, false, true>, attr, sm) != cudaSuccess ||
+            cudaFuncSetAttribute(fw_phase3_f32x2<S, true, true>, attr, sm) != cudaSuccess ||
+            cudaFuncSetAttribute(fw_phase3_f32x2<S, false, false>, attr, sm) != cudaSuccess ||
+            cudaFuncSetAttribute(fw_phase3_f32x2<S, true, false>, attr, sm) != cudaSuccess)
+          return APSP_ECUDA;
+      }
     }
     setup_done_mask |= 1 << (dev & 31);
   }
@@ -77,10 +102,18 @@ static int run_rounds(const RunArgs &a) {
   const bool generic_only = (a.flags & APSP_FLAG_GENERIC) != 0;
   cudaStream_t st = a.stream;
 
-  CUtensorMap mA, mB;
-  bool use_tma = false;
+  CUtensorMap mA, mB, mBp;
+  bool use_tma = false, use_packed = false;
+  T *bp = nullptr;
+  const int64_t np = (int64_t)R * S;
   if constexpr (HAS_TMA) {
     use_tma = a.tma_ok && !generic_only && R > 1 && make_panel_maps<T, S>(d, n, ld, &mA, &mB);
+    if constexpr (std::is_same<T, float>::value) {
+      use_packed = use_tma && a.ws && a.ws_bytes >= interleaved_panel_bytes(n, S) &&
+                   reinterpret_cast<uintptr_t>(a.ws) % 256 == 0 &&
+                   make_interleaved_map<S>(static_cast<float *>(a.ws), np, &mBp);
+      if (use_packed) bp = static_cast<T *>(a.ws);
+    }
   }
 
   auto ev = [&](int64_t idx) -> bool {
@@ -91,18 +124,53 @@ static int run_rounds(const RunArgs &a) {
   for (int b = 0; b < R; ++b) {
     const int last = (b == R - 1) ? 1 : 0;
     if (!ev(4ll * b)) return APSP_ECUDA;
-    fw_phase1<T, S, K::NT12><<<1, K::NT12, K::SM1, st>>>(d, n, ld, b, last);
+    fw_phase1<T, S><<<1, K::NT1, 0, st>>>(d, n, ld, b, last);
     if (!ev(4ll * b + 1)) return APSP_ECUDA;
-    if (R > 1) fw_phase2<T, S, K::NT12><<<2 * (R - 1), K::NT12, K::SM2, st>>>(d, n, ld, b, R, last);
+    const bool full_k = (int64_t)(b + 1) * S <= n;
+    T *bp_round = (use_packed && full_k) ? bp : nullptr;
+    if (R > 1) {
+      bool launched2 = false;
+      if constexpr (HAS_TMA) {
+        if (use_tma && full_k) {
+          fw_tile_tma<T, S, 1><<<2 * (R - 1), P3Tma<S>::TPB, P3Tma<S>::SMEM, st>>>(
+              mA, mB, d, n, ld, b, R, last, reverse, bp_round, 2 * np, a.err);
+          launched2 = true;
+        }
+      }
+      if (!launched2)
+        fw_phase2<T, S, K::NT2><<<2 * (R - 1), K::NT2, K::SM2, st>>>(d, n, ld, b, R, last, bp_round, 2 * np);
+    }
     if (!ev(4ll * b + 2)) return APSP_ECUDA;
     if (R > 1) {
       const dim3 grid(R - 1, R - 1);
-      const bool full_k = (int64_t)(b + 1) * S <= n;
       bool launched = false;
+      if constexpr (std::is_same<T, float>::value) {
+        if (bp_round) {
+          // interior tiles (all rows/columns inside the matrix), then the
+          // edge tiles of a ragged matrix
+          const int ragged = (n % S) != 0 ? 1 : 0;
+          const dim3 gi(R - 1 - ragged, R - 1 - ragged);
+          const int ne = ragged ? 2 * R - 3 : 0;
+          const int tpb = P3Tma<S>::TPB, sm = P3Tma<S>::SMEM;
+          if (gi.x > 0) {
+            if (reverse)
+              fw_phase3_f32x2<S, true, true><<<gi, tpb, sm, st>>>(mA, mBp, d, n, ld, b, R, a.err);
+            else
+              fw_phase3_f32x2<S, false, true><<<gi, tpb, sm, st>>>(mA, mBp, d, n, ld, b, R, a.err);
+          }
+          if (ne > 0) {
+            if (reverse)
+              fw_phase3_f32x2<S, true, false><<<ne, tpb, sm, st>>>(mA, mBp, d, n, ld, b, R, a.err);
+            else
+              fw_phase3_f32x2<S, false, false><<<ne, tpb, sm, st>>>(mA, mBp, d, n, ld, b, R, a.err);
+          }
+          launched = true;
+        }
+      }
       if constexpr (HAS_TMA) {
-        if (use_tma && full_k) {
-          fw_phase3_tma<T, S><<<grid, P3Tma<S>::TPB, P3Tma<S>::SMEM, st>>>(mA, mB, d, n, ld, b, last, reverse,
-                                                                           a.err);
+        if (!launched && use_tma && full_k) {
+          fw_tile_tma<T, S, 0><<<grid, P3Tma<S>::TPB, P3Tma<S>::SMEM, st>>>(mA, mB, d, n, ld, b, R, last, reverse,
+                                                                            (T *)nullptr, 0, a.err);
           launched = true;
         }
       }

@@ -19,48 +19,79 @@
 
 #include "apsp_common.cuh"
 
+#include <type_traits>
+
 namespace apsp {
 
 // ------------------------------------------------------------------ phase 1
-// One CTA; the s x s diagonal tile in shared memory; s barriers.
-// Within step k, row k and column k of the tile do not change (d_kk >= 0), so
-// the in-place update needs no second buffer.
-template <typename T, int S, int NT>
-__global__ void __launch_bounds__(NT) fw_phase1(T *__restrict__ d, int64_t n, int64_t ld, int b, int last) {
+// One CTA closes the diagonal tile (b, b): s sequential k steps, each a rank-1
+// update x_ij <- min(x_ij, x_ik + x_kj) of the whole tile.
+// The tile lives in registers, a 4 x 4 block per thread ((s/4)^2 threads);
+// only row k and column k travel through shared memory.  Within step k, row k
+// and column k do not change (d_kk >= 0), so the owners of row/column k+1
+// publish them right after their own step-k update, into the other half of a
+// double buffer: one barrier per step.
+template <typename T, int S>
+__global__ void __launch_bounds__((S / 4) * (S / 4)) fw_phase1(T *__restrict__ d, int64_t n, int64_t ld, int b,
+                                                               int last) {
   using C = typename Arith<T>::C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *X = reinterpret_cast<C *>(smem_raw);
-  constexpr int E = S * S / NT;   // elements per thread
-  constexpr int RS = NT / S;      // row stride between a thread's elements
-  const int j = threadIdx.x % S;
-  const int i0 = threadIdx.x / S;
+  constexpr int Q = S / 4;  // threads per dimension
+  __shared__ __align__(16) C rowbuf[2][S];
+  __shared__ __align__(16) C colbuf[2][S];
+  const int tx = threadIdx.x % Q, ty = threadIdx.x / Q;
   const int64_t base = (int64_t)b * S;
-  const bool cj = base + j < n;
-
+  C x[4][4];
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int i = i0 + RS * r;
-    const bool ok = cj && base + i < n;
-    X[i * S + j] = ok ? Arith<T>::load(d[(base + i) * ld + base + j]) : Arith<T>::inf();
-  }
-  __syncthreads();
-  for (int k = 0; k < S; ++k) {
-    const C xkj = X[k * S + j];
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int i = i0 + RS * r;
-      X[i * S + j] = Arith<T>::relax(X[i * S + j], X[i * S + k], xkj);
+    for (int c = 0; c < 4; ++c) {
+      const int64_t gi = base + 4 * ty + a, gj = base + 4 * tx + c;
+      x[a][c] = (gi < n && gj < n) ? Arith<T>::load(d[gi * ld + gj]) : Arith<T>::inf();
     }
-    __syncthreads();
-  }
+  if (ty == 0) {
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int i = i0 + RS * r;
-    if (cj && base + i < n) {
-      const C v = X[i * S + j];
-      d[(base + i) * ld + base + j] = last ? Arith<T>::finish(v) : (T)v;
+    for (int c = 0; c < 4; ++c) rowbuf[0][4 * tx + c] = x[0][c];
+  }
+  if (tx == 0) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) colbuf[0][4 * ty + a] = x[a][0];
+  }
+  for (int kq = 0; kq < Q; ++kq) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = 4 * kq + u;
+      __syncthreads();
+      C rk[4], ck[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rk[c] = rowbuf[k & 1][4 * tx + c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ck[a] = colbuf[k & 1][4 * ty + a];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[a][c] = Arith<T>::relax(x[a][c], ck[a], rk[c]);
+      // publish row / column k + 1 (local index (u + 1) % 4 of its owners)
+      const int k1 = k + 1;
+      if (k1 < S) {
+        const int owner = k1 >> 2;
+        if (ty == owner) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) rowbuf[k1 & 1][4 * tx + c] = x[(u + 1) & 3][c];
+        }
+        if (tx == owner) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) colbuf[k1 & 1][4 * ty + a] = x[a][(u + 1) & 3];
+        }
+      }
     }
   }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t gi = base + 4 * ty + a, gj = base + 4 * tx + c;
+      if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(x[a][c]) : (T)x[a][c];
+    }
 }
 
 // ------------------------------------------------------------------ phase 2
@@ -69,8 +100,14 @@ __global__ void __launch_bounds__(NT) fw_phase1(T *__restrict__ d, int64_t n, in
 // and the panel tile X.
 //   row panel:    x_ij <- min(x_ij, D_ik + x_kj)
 //   column panel: x_ij <- min(x_ij, x_ik + D_kj)
+//
+// With bp != nullptr the row panel tiles are also stored, k-pair interleaved,
+// into bp: element (k, j) of the pivot row block goes to
+// bp[(k / 2) * bp_ld + 2 * j + (k % 2)] (j = global column, padding included),
+// the layout the packed fp32 phase-3 kernel reads.
 template <typename T, int S, int NT>
-__global__ void __launch_bounds__(NT) fw_phase2(T *__restrict__ d, int64_t n, int64_t ld, int b, int R, int last) {
+__global__ void __launch_bounds__(NT) fw_phase2(T *__restrict__ d, int64_t n, int64_t ld, int b, int R, int last,
+                                                T *__restrict__ bp, int64_t bp_ld) {
   using C = typename Arith<T>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *D = reinterpret_cast<C *>(smem_raw);
@@ -121,6 +158,13 @@ __global__ void __launch_bounds__(NT) fw_phase2(T *__restrict__ d, int64_t n, in
     if (r0 + i < n && c0 + j < n) {
       const C v = X[i * S + j];
       d[(r0 + i) * ld + c0 + j] = last ? Arith<T>::finish(v) : (T)v;
+    }
+  }
+  if (bp && row_panel) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int i = i0 + RS * r;
+      bp[(int64_t)(i >> 1) * bp_ld + 2 * (c0 + j) + (i & 1)] = (T)X[i * S + j];
     }
   }
 }
@@ -179,19 +223,42 @@ __global__ void __launch_bounds__(256) fw_phase3_generic(T *__restrict__ d, int6
     }
 }
 
-// --------------------------------------------------- phase 3 (TMA-staged)
-// 4-byte element types, full k-block (k0 + S <= n), 16-byte aligned rows.
+// ------------------------------------------- phases 2 and 3 (TMA-staged)
+// One kernel updates a set of S x S tiles C = (I, J) with
+//     c_ij <- min(c_ij, min_{k in block b} a_ik + b_kj),
+//     a = tile (I, b) of the matrix, b = tile (b, J) of the matrix,
+// for 4-byte element types, a full k-block (k0 + S <= n) and 16-byte aligned
+// rows.
+//   phase 3 (MODE 0): the doubly dependent tiles I != b, J != b; grid
+//            (R-1, R-1).  Their operands are final for the stage.
+//   phase 2 (MODE 1): the singly dependent tiles; blockIdx.x < R-1 takes the
+//            row panel tile (b, J), the rest the column panel tile (I, b).
+//            After phase 1 the diagonal tile D is closed (its own shortest
+//            paths, zero diagonal), and the k-sequential loop of Fig. 2 on a
+//            row panel tile X reaches exactly min_k D_ik + X_kj: a path from
+//            i to j through block b leaves the block once, at its last
+//            vertex k.  So the row panel is the min-plus product D (x) X and
+//            the column panel X (x) D, both of the form above, with a = D or
+//            b = D.  A CTA reads its own tile as an operand; all its TMA
+//            reads complete before its single store at the end.
+//            (Integers: exactly the sequential result; fp32: the same
+//            shortest-path value up to the association of the additions.)
 //
 // CTA tile S x S, (S/8)^2 threads, 8 x 8 register micro-tile per thread:
 // rows ty + G*r (r < 8), columns h*S/2 + 4*tx + c (h < 2, c < 4), G = S/8.
-// The two panels stream through shared memory in k-slices of 32 (the staged
-// load of Sec. 4.2) filled by TMA into a 2-deep ring guarded by mbarriers:
-//   A slice = column panel rows of tile I x 32 k's, 128-byte swizzled rows
-//             (16-byte chunk c of row i stored at chunk c ^ (i % 8)), so the
-//             8 rows a warp reads for one k-quad hit distinct banks;
+// The operands stream through shared memory in k-slices of 32 (the staged
+// load of Sec. 4.2), filled by TMA into a 2-deep ring guarded by mbarriers:
+//   A slice = rows of tile I x 32 k's, 128-byte swizzled rows (16-byte chunk
+//             c of row i stored at chunk c ^ (i % 8)), so the 8 rows a warp
+//             reads for one k-quad hit distinct banks;
 //   B slice = 32 k's x S columns of tile J, plain row-major.
 // The C tile goes global -> registers with 128-bit loads issued before the
 // first wait, so they overlap the first TMA copies.
+//
+// With bp != nullptr (phase 2, fp32) the row panel tiles are also written,
+// k-pair interleaved, to bp: element (k, j) of the pivot row block goes to
+// bp[(k / 2) * bp_ld + 2 * j + (k % 2)] (j = global column, padding
+// included), the layout the packed fp32 phase-3 kernel reads.
 template <int S> struct P3Tma {
   static constexpr int G = S / 8;
   static constexpr int TPB = G * G;
@@ -204,7 +271,6 @@ template <int S> struct P3Tma {
   static constexpr int MIN_BLOCKS = S == 128 ? 2 : 6;
 };
 
-// 128-bit shared/global accesses of four consecutive 4-byte elements.
 template <typename T>
 __device__ __forceinline__ void ld4(const T *p, T &x0, T &x1, T &x2, T &x3);
 template <>
@@ -227,11 +293,30 @@ template <>
 __device__ __forceinline__ void st4<float>(float *p, float x0, float x1, float x2, float x3) {
   *reinterpret_cast<float4 *>(p) = make_float4(x0, x1, x2, x3);
 }
+// Shared-memory loads the compiler may not merge or hoist across the k-pair
+// loop (keeps the 64 accumulators within two CTAs per SM worth of registers).
+template <typename T>
+__device__ __forceinline__ void lds2(const T *p, T &x0, T &x1) {
+  uint32_t a, b;
+  asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "r"(smem_u32(p)));
+  x0 = *reinterpret_cast<T *>(&a);
+  x1 = *reinterpret_cast<T *>(&b);
+}
+template <typename T>
+__device__ __forceinline__ void lds4(const T *p, T &x0, T &x1, T &x2, T &x3) {
+  uint32_t a, b, c, e;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(a), "=r"(b), "=r"(c), "=r"(e) : "r"(smem_u32(p)));
+  x0 = *reinterpret_cast<T *>(&a);
+  x1 = *reinterpret_cast<T *>(&b);
+  x2 = *reinterpret_cast<T *>(&c);
+  x3 = *reinterpret_cast<T *>(&e);
+}
 
-template <typename T, int S>
+template <typename T, int S, int MODE>
 __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
-    fw_phase3_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  T *__restrict__ d, int64_t n, int64_t ld, int b, int last, int reverse, int *err) {
+    fw_tile_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                T *__restrict__ d, int64_t n, int64_t ld, int b, int R, int last, int reverse,
+                T *__restrict__ bp, int64_t bp_ld, int *err) {
   using P = P3Tma<S>;
   constexpr int G = P::G;
   constexpr int KS = P::KS;
@@ -244,7 +329,16 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
 
   const int tid = threadIdx.x;
   const int tx = tid % G, ty = tid / G;
-  const int It = skip_pivot(blockIdx.y, b), Jt = skip_pivot(blockIdx.x, b);
+  int It, Jt;
+  bool row_panel = false;
+  if (MODE == 0) {
+    It = skip_pivot(blockIdx.y, b);
+    Jt = skip_pivot(blockIdx.x, b);
+  } else {
+    row_panel = (int)blockIdx.x < R - 1;
+    It = row_panel ? b : skip_pivot(blockIdx.x - (R - 1), b);
+    Jt = row_panel ? skip_pivot(blockIdx.x, b) : b;
+  }
   const int64_t I0 = (int64_t)It * S, J0 = (int64_t)Jt * S;
   const int k0 = b * S;
 
@@ -287,29 +381,57 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
   }
 
   bool timed_out = false;
+  const int sw = ty & 7;  // swizzle phase of every row this thread reads
   for (int s = 0; s < P::NSL; ++s) {
     const int st = s % P::STAGES;
     if (!mbar_wait_bounded(&full[st], (s / P::STAGES) & 1)) timed_out = true;
-    const T *A = As + st * (S * KS);
-    const T *B = Bs + st * (KS * S);
-    const int sw = ty & 7;  // swizzle phase of every row this thread reads
+    const T *A = As + st * (S * KS) + ty * KS;
+    const T *B = Bs + st * (KS * S) + 4 * tx;
+    if constexpr (std::is_same<T, float>::value) {
+      // fp32 (fadd + fmin, 2 issue slots per relaxation): one k-pair per
+      // iteration, operands loaded per iteration, to stay spill-free.
+#pragma unroll 1
+      for (int pi = 0; pi < KS / 2; ++pi) {
+        const int p = reverse ? KS / 2 - 1 - pi : pi;  // k-pair (2p, 2p + 1) of the slice
+        const int aoff = (((p >> 1) ^ sw) << 2) + ((p & 1) << 1);
+        T a[8][2];
 #pragma unroll
-    for (int qi = 0; qi < KS / 4; ++qi) {
-      const int q = reverse ? KS / 4 - 1 - qi : qi;
-      T a[8][4];
+        for (int r = 0; r < 8; ++r) lds2<T>(A + G * r * KS + aoff, a[r][0], a[r][1]);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) ld4<T>(A + (ty + G * r) * KS + ((q ^ sw) << 2), a[r][0], a[r][1], a[r][2], a[r][3]);
+        for (int ui = 0; ui < 2; ++ui) {
+          const int u = reverse ? 1 - ui : ui;
+          const T *brow = B + (2 * p + u) * S;
+          T bv[8];
+          lds4<T>(brow, bv[0], bv[1], bv[2], bv[3]);
+          lds4<T>(brow + S / 2, bv[4], bv[5], bv[6], bv[7]);
 #pragma unroll
-      for (int ui = 0; ui < 4; ++ui) {
-        const int u = reverse ? 3 - ui : ui;
-        const T *brow = B + (4 * q + u) * S + 4 * tx;
-        T bv[8];
-        ld4<T>(brow, bv[0], bv[1], bv[2], bv[3]);
-        ld4<T>(brow + S / 2, bv[4], bv[5], bv[6], bv[7]);
+          for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+            for (int c = 0; c < 8; ++c) acc[r][c] = Arith<T>::relax(acc[r][c], a[r][u], bv[c]);
+        }
+      }
+    } else {
+      // int32 (one DPX add-min per relaxation on the half-rate pipe): the
+      // fully unrolled slice lets the compiler run the shared loads far
+      // ahead of their use; issue slots are not the limit here.
 #pragma unroll
-          for (int c = 0; c < 8; ++c) acc[r][c] = Arith<T>::relax(acc[r][c], a[r][u], bv[c]);
+      for (int qi = 0; qi < KS / 4; ++qi) {
+        const int q = reverse ? KS / 4 - 1 - qi : qi;
+        T a[8][4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) ld4<T>(A + G * r * KS + ((q ^ sw) << 2), a[r][0], a[r][1], a[r][2], a[r][3]);
+#pragma unroll
+        for (int ui = 0; ui < 4; ++ui) {
+          const int u = reverse ? 3 - ui : ui;
+          const T *brow = B + (4 * q + u) * S;
+          T bv[8];
+          ld4<T>(brow, bv[0], bv[1], bv[2], bv[3]);
+          ld4<T>(brow + S / 2, bv[4], bv[5], bv[6], bv[7]);
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = Arith<T>::relax(acc[r][c], a[r][u], bv[c]);
+        }
       }
     }
     // every thread is done with stage st: refill it with slice s + STAGES
@@ -346,6 +468,199 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
         if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(acc[r][c]) : acc[r][c];
       }
   }
+  if (MODE == 1 && bp && row_panel) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = ty + G * r;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int64_t j = J0 + (c / 4) * (S / 2) + 4 * tx + (c % 4);
+        bp[(int64_t)(i >> 1) * bp_ld + 2 * j + (i & 1)] = acc[r][c];
+      }
+    }
+  }
+}
+
+// ------------------------------------------- phase 3, fp32 packed form
+// Same tiling and TMA ring as fw_tile_tma, but two k's are consumed per
+// instruction pair: a packed add.f32x2 forms (a_ik + b_kj, a_ik' + b_k'j)
+// for k' = k + 1 and a three-input min folds both into the accumulator,
+// i.e. acc <- min(acc, a_ik + b_kj, a_ik' + b_k'j).  Each addition is rounded
+// once and the minimum is exact, so the result is bit-identical to the
+// one-k-at-a-time form.
+// The B operand comes from the k-pair interleaved copy of the row panel
+// written by phase 2 (slice = 16 k-pairs x 2S floats), so that one 128-bit
+// load yields the (k, k+1) pairs of two adjacent columns.  Thread columns:
+// j = 2 (tx + G m) + e, m < 4, e < 2.
+//
+// FULL = true: every row and column of the tile is inside the matrix (the
+// interior tiles); FULL = false: masked loads/stores, blockIdx.x enumerates
+// the edge tiles (last tile row, then last tile column) of a ragged matrix.
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// (a.x + b.x, a.y + b.y), each rounded to nearest: one packed add.f32x2.
+__device__ __forceinline__ float2 add2f(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Tile (I, J) of a phase-3 CTA.  Interior launches use blockIdx directly;
+// edge launches number the ragged last tile row (x = 0..R-2) and then the
+// last tile column (y = 0..R-3) in blockIdx.x.
+template <bool FULL>
+__device__ __forceinline__ void phase3_tile(int b, int R, int &It, int &Jt) {
+  int bx, by;
+  if (FULL) {
+    bx = blockIdx.x;
+    by = blockIdx.y;
+  } else {
+    const int t = blockIdx.x;
+    if (t < R - 1) {
+      by = R - 2;
+      bx = t;
+    } else {
+      bx = R - 2;
+      by = t - (R - 1);
+    }
+  }
+  It = skip_pivot(by, b);
+  Jt = skip_pivot(bx, b);
+}
+
+template <int S, bool REVERSE, bool FULL>
+__global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
+    fw_phase3_f32x2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBp,
+                    float *__restrict__ d, int64_t n, int64_t ld, int b, int R, int *err) {
+  using P = P3Tma<S>;
+  constexpr int G = P::G;
+  constexpr int KS = P::KS;
+  constexpr int KP = KS / 2;  // k-pairs per slice
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float *As = reinterpret_cast<float *>(base);
+  float *Bs = reinterpret_cast<float *>(base + P::STAGES * P::A_BYTES);
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + P::STAGES * (P::A_BYTES + P::B_BYTES));
+
+  const int tid = threadIdx.x;
+  const int tx = tid % G, ty = tid / G;
+  int It, Jt;
+  phase3_tile<FULL>(b, R, It, Jt);
+  const int k0 = b * S;
+
+  if (tid == 0) {
+    prefetch_tensormap(&tmA);
+    prefetch_tensormap(&tmBp);
+#pragma unroll
+    for (int s = 0; s < P::STAGES; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < P::STAGES && s < P::NSL; ++s) {
+      mbar_arrive_expect_tx(&full[s], P::A_BYTES + P::B_BYTES);
+      tma_load_2d(As + s * (S * KS), &tmA, &full[s], k0 + s * KS, It * S);
+      tma_load_2d(Bs + s * (KS * S), &tmBp, &full[s], 2 * Jt * S, s * KP);
+    }
+  }
+
+  // C tile -> registers.  The addresses are derived from (It, Jt, ty, tx)
+  // here and again after the main loop from copies the compiler cannot see
+  // through, so that no address is kept live across the loop.
+  float acc[8][8];
+  uint64_t cbase = reinterpret_cast<uint64_t>(d + ((int64_t)It * S + ty) * ld + (int64_t)Jt * S + 2 * tx);
+  const int64_t rstride = (int64_t)G * ld * (int64_t)sizeof(float);
+  int rows_left = 0, cols_left = 0;  // (masked form) rows/cols of the tile inside the matrix, from this thread
+  if (!FULL) {
+    rows_left = (int)(n - ((int64_t)It * S + ty));
+    cols_left = (int)(n - ((int64_t)Jt * S + 2 * tx));
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float *pc = reinterpret_cast<const float *>(cbase + r * rstride + 8 * G * m);
+      if (FULL) {
+        const float2 v = *reinterpret_cast<const float2 *>(pc);
+        acc[r][2 * m] = v.x;
+        acc[r][2 * m + 1] = v.y;
+      } else {
+        const bool rok = G * r < rows_left;
+        acc[r][2 * m] = (rok && 2 * G * m < cols_left) ? pc[0] : Arith<float>::inf();
+        acc[r][2 * m + 1] = (rok && 2 * G * m + 1 < cols_left) ? pc[1] : Arith<float>::inf();
+      }
+    }
+
+  bool timed_out = false;
+  const int sw = ty & 7;
+  for (int s = 0; s < P::NSL; ++s) {
+    const int st = s % P::STAGES;
+    if (!mbar_wait_bounded(&full[st], (s / P::STAGES) & 1)) timed_out = true;
+    const float *A = As + st * (S * KS) + ty * KS;
+    const float *B = Bs + st * (KS * S) + 4 * tx;
+    // One k-pair per iteration.  The loop is deliberately not unrolled: with
+    // the next pair's operands hoisted into the current iteration the 64
+    // accumulators no longer fit the 128-register budget of two CTAs per SM.
+#pragma unroll 1
+    for (int pi = 0; pi < KP; ++pi) {
+      const int p = REVERSE ? KP - 1 - pi : pi;
+      const int aoff = (((p >> 1) ^ sw) << 2) + ((p & 1) << 1);  // swizzled (k, k+1) of a row
+      float2 ap[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                     : "=f"(ap[r].x), "=f"(ap[r].y)
+                     : "r"(smem_u32(A + G * r * KS + aoff)));
+      float4 bq[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(bq[m].x), "=f"(bq[m].y), "=f"(bq[m].z), "=f"(bq[m].w)
+                     : "r"(smem_u32(B + p * (2 * S) + 4 * G * m)));
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float2 s0 = add2f(ap[r], make_float2(bq[m].x, bq[m].y));
+          const float2 s1 = add2f(ap[r], make_float2(bq[m].z, bq[m].w));
+          acc[r][2 * m] = min3f(acc[r][2 * m], s0.x, s0.y);
+          acc[r][2 * m + 1] = min3f(acc[r][2 * m + 1], s1.x, s1.y);
+        }
+    }
+    if (__syncthreads_or(timed_out)) {
+      if (tid == 0) atomicCAS(err, 0, (int)kDevTimeoutTma);
+      return;
+    }
+    if (tid == 0 && s + P::STAGES < P::NSL) {
+      const int s2 = s + P::STAGES;
+      mbar_arrive_expect_tx(&full[st], P::A_BYTES + P::B_BYTES);
+      tma_load_2d(As + st * (S * KS), &tmA, &full[st], k0 + s2 * KS, It * S);
+      tma_load_2d(Bs + st * (KS * S), &tmBp, &full[st], 2 * Jt * S, s2 * KP);
+    }
+  }
+
+  int It2 = It, Jt2 = Jt, ty2 = ty, tx2 = tx;
+  asm volatile("" : "+r"(It2), "+r"(Jt2), "+r"(ty2), "+r"(tx2));
+  cbase = reinterpret_cast<uint64_t>(d + ((int64_t)It2 * S + ty2) * ld + (int64_t)Jt2 * S + 2 * tx2);
+  if (!FULL) {
+    rows_left = (int)(n - ((int64_t)It2 * S + ty2));
+    cols_left = (int)(n - ((int64_t)Jt2 * S + 2 * tx2));
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float *pc = reinterpret_cast<float *>(cbase + r * rstride + 8 * G * m);
+      if (FULL) {
+        *reinterpret_cast<float2 *>(pc) = make_float2(acc[r][2 * m], acc[r][2 * m + 1]);
+      } else {
+        const bool rok = G * r < rows_left;
+        if (rok && 2 * G * m < cols_left) pc[0] = acc[r][2 * m];
+        if (rok && 2 * G * m + 1 < cols_left) pc[1] = acc[r][2 * m + 1];
+      }
+    }
 }
 
 }  // namespace apsp

@@ -1,11 +1,14 @@
 // Roofline calibration for the min-plus relaxation (apsp_ubench_minplus).
 //
-// Each thread keeps the same 8 x 8 register micro-tile as the phase-3 kernel
-// and applies acc[r][c] <- min(acc[r][c], a[r] + b[c]) with no memory traffic
-// in the loop.  An empty asm statement marks a[] and b[] as rewritten every
-// iteration, so the compiler can neither fold repeated minima nor hoist the
-// additions, at no instruction cost.  The measured relaxations per second,
-// divided by SMs x clock, give lanes per clock per SM for each form.
+// Each form runs the phase-3 inner loop of one element type on operands that
+// come from shared memory every k step, exactly as in the kernels: 256
+// threads, an 8 x 8 register micro-tile per thread, a 32-k slice of the two
+// panels (A: 128 rows x 32 k's with 128-byte swizzled rows, B: 32 k's x 128
+// columns, or 16 k-pairs x 256 interleaved floats for the packed fp32 form),
+// swept `iters` times.  Real loads matter: register-only loops let the
+// compiler hoist the additions out of the loop and measure the minimum alone.
+// Relaxations per second divided by SMs x clock give relaxations per clock
+// per SM for each instruction form.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -14,10 +17,7 @@
 
 namespace {
 
-template <typename T> __device__ __forceinline__ void opaque(T &x);
-template <> __device__ __forceinline__ void opaque<int32_t>(int32_t &x) { asm volatile("" : "+r"(x)); }
-template <> __device__ __forceinline__ void opaque<uint32_t>(uint32_t &x) { asm volatile("" : "+r"(x)); }
-template <> __device__ __forceinline__ void opaque<float>(float &x) { asm volatile("" : "+f"(x)); }
+constexpr int kRows = 128, kKs = 32, kCols = 128;
 
 __device__ __forceinline__ int32_t relax_dpx(int32_t acc, int32_t a, int32_t b) { return __viaddmin_s32(a, b, acc); }
 __device__ __forceinline__ int32_t relax_addmin(int32_t acc, int32_t a, int32_t b) {
@@ -30,110 +30,177 @@ __device__ __forceinline__ float relax_f32(float acc, float a, float b) { return
 __device__ __forceinline__ uint32_t relax_s16x2(uint32_t acc, uint32_t a, uint32_t b) {
   return __viaddmin_s16x2(a, b, acc);
 }
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
 
-// form 0/3: int32, form 1: fp32, form 2: int16x2
+template <typename T> __device__ __forceinline__ T fill(int i);
+template <> __device__ __forceinline__ int32_t fill<int32_t>(int i) { return i % 997; }
+template <> __device__ __forceinline__ uint32_t fill<uint32_t>(int i) { return (uint32_t)(i % 991) * 0x10001u; }
+template <> __device__ __forceinline__ float fill<float>(int i) { return (float)(i % 997) * 0.001f; }
+
+// forms 0, 1, 2, 3: one k per step (the integer / unpacked kernels' loop:
+// k-quads of A by 128-bit loads, two 128-bit loads of B per k).
 template <typename T, int FORM>
-__global__ void ubench_kernel(int64_t iters, T *sink) {
-  T a[8], b[8], acc[8][8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    a[r] = (T)(threadIdx.x + r);
-    b[r] = (T)(blockIdx.x + 3 * r);
-  }
+__global__ void __launch_bounds__(256, 2) ubench_kstep(int64_t iters, T *sink) {
+  __shared__ __align__(16) T As[kRows * kKs];
+  __shared__ __align__(16) T Bs[kKs * kCols];
+  for (int i = threadIdx.x; i < kRows * kKs; i += blockDim.x) As[i] = fill<T>(i);
+  for (int i = threadIdx.x; i < kKs * kCols; i += blockDim.x) Bs[i] = fill<T>(i + 7);
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16, sw = ty & 7;
+  const T *A = As + ty * kKs;
+  const T *B = Bs + 4 * tx;
+  T acc[8][8];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = (T)(1 << 20);
+    for (int c = 0; c < 8; ++c) acc[r][c] = fill<T>(1000 + r + c);
+#pragma unroll 1
   for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll 2
+    for (int q = 0; q < kKs / 4; ++q) {
+      T a[8][4];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      opaque<T>(a[r]);
-      opaque<T>(b[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if constexpr (FORM == 0) acc[r][c] = relax_dpx(acc[r][c], a[r], b[c]);
-        if constexpr (FORM == 1) acc[r][c] = relax_f32(acc[r][c], a[r], b[c]);
-        if constexpr (FORM == 2) acc[r][c] = relax_s16x2(acc[r][c], a[r], b[c]);
-        if constexpr (FORM == 3) acc[r][c] = relax_addmin(acc[r][c], a[r], b[c]);
+      for (int r = 0; r < 8; ++r) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(A + 16 * r * kKs + ((q ^ sw) << 2));
+        a[r][0] = __builtin_bit_cast(T, v.x);
+        a[r][1] = __builtin_bit_cast(T, v.y);
+        a[r][2] = __builtin_bit_cast(T, v.z);
+        a[r][3] = __builtin_bit_cast(T, v.w);
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint4 b0 = *reinterpret_cast<const uint4 *>(B + (4 * q + u) * kCols);
+        const uint4 b1 = *reinterpret_cast<const uint4 *>(B + (4 * q + u) * kCols + kCols / 2);
+        const T bv[8] = {__builtin_bit_cast(T, b0.x), __builtin_bit_cast(T, b0.y), __builtin_bit_cast(T, b0.z),
+                         __builtin_bit_cast(T, b0.w), __builtin_bit_cast(T, b1.x), __builtin_bit_cast(T, b1.y),
+                         __builtin_bit_cast(T, b1.z), __builtin_bit_cast(T, b1.w)};
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            if constexpr (FORM == 0) acc[r][c] = relax_dpx(acc[r][c], a[r][u], bv[c]);
+            if constexpr (FORM == 1) acc[r][c] = relax_f32(acc[r][c], a[r][u], bv[c]);
+            if constexpr (FORM == 2) acc[r][c] = relax_s16x2(acc[r][c], a[r][u], bv[c]);
+            if constexpr (FORM == 3) acc[r][c] = relax_addmin(acc[r][c], a[r][u], bv[c]);
+          }
+      }
+    }
   }
   T s = acc[0][0];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) s = (r + c) ? (acc[r][c] < s ? acc[r][c] : s) : s;
+    for (int c = 0; c < 8; ++c) s = acc[r][c] < s ? acc[r][c] : s;
   sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-// form 4: fp32 with packed f32x2 additions (two k's at once) and a three-input
-// minimum: acc <- min(acc, a0 + b0, a1 + b1), 2 relaxations per 2 instructions.
-__global__ void ubench_f32x2(int64_t iters, float *sink) {
-  float a0[8], a1[8], b0[8], b1[8], acc[8][8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    a0[r] = threadIdx.x + r;
-    a1[r] = threadIdx.x - r;
-    b0[r] = blockIdx.x + 3 * r;
-    b1[r] = blockIdx.x - 3 * r;
-  }
+// form 4: the packed fp32 loop: per k-pair, 8 (k, k+1) pairs of A (64-bit
+// loads) and 4 column-pair quads of the k-pair interleaved B (128-bit loads),
+// then acc <- min(acc, a_k + b_k, a_k' + b_k') with one add.f32x2 and one
+// three-input min per (row, column).
+// form 5: int32, two adds + one three-input minimum per (row, column, k-pair).
+template <int FORM>
+__global__ void __launch_bounds__(256, 2) ubench_kpair(int64_t iters, void *sinkv) {
+  __shared__ __align__(16) float As[kRows * kKs];
+  __shared__ __align__(16) float Bs[(kKs / 2) * 2 * kCols];
+  for (int i = threadIdx.x; i < kRows * kKs; i += blockDim.x) As[i] = fill<float>(i);
+  for (int i = threadIdx.x; i < kKs * kCols; i += blockDim.x) Bs[i] = fill<float>(i + 7);
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16, sw = ty & 7;
+  const float *A = As + ty * kKs;
+  const float *B = Bs + 4 * tx;
+  float acc[8][8];
+  int32_t iacc[8][8];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = 1e20f;
-  for (int64_t it = 0; it < iters; ++it) {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      opaque<float>(a0[r]);
-      opaque<float>(a1[r]);
-      opaque<float>(b0[r]);
-      opaque<float>(b1[r]);
+    for (int c = 0; c < 8; ++c) {
+      acc[r][c] = 1e20f;
+      iacc[r][c] = 1 << 29;
     }
+#pragma unroll 1
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll 1
+    for (int p = 0; p < kKs / 2; ++p) {
+      const int aoff = (((p >> 1) ^ sw) << 2) + ((p & 1) << 1);
+      float2 ap[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                     : "=f"(ap[r].x), "=f"(ap[r].y)
+                     : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(A + 16 * r * kKs + aoff))));
+      float4 bq[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(bq[m].x), "=f"(bq[m].y), "=f"(bq[m].z), "=f"(bq[m].w)
+                     : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(B + p * 2 * kCols + 64 * m))));
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          if constexpr (FORM == 4) {
+            const float2 s0 = __fadd2_rn(ap[r], make_float2(bq[m].x, bq[m].y));
+            const float2 s1 = __fadd2_rn(ap[r], make_float2(bq[m].z, bq[m].w));
+            acc[r][2 * m] = min3f(acc[r][2 * m], s0.x, s0.y);
+            acc[r][2 * m + 1] = min3f(acc[r][2 * m + 1], s1.x, s1.y);
+          } else {
+            const int32_t a0 = __float_as_int(ap[r].x), a1 = __float_as_int(ap[r].y);
+            iacc[r][2 * m] = __vimin3_s32(iacc[r][2 * m], a0 + __float_as_int(bq[m].x), a1 + __float_as_int(bq[m].y));
+            iacc[r][2 * m + 1] =
+                __vimin3_s32(iacc[r][2 * m + 1], a0 + __float_as_int(bq[m].z), a1 + __float_as_int(bq[m].w));
+          }
+        }
+    }
+  }
+  if constexpr (FORM == 4) {
+    float s = 1e30f;
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        uint64_t av, bv, sv;
-        asm("mov.b64 %0, {%1, %2};" : "=l"(av) : "f"(a0[r]), "f"(a1[r]));
-        asm("mov.b64 %0, {%1, %2};" : "=l"(bv) : "f"(b0[c]), "f"(b1[c]));
-        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(sv) : "l"(av), "l"(bv));
-        float s0, s1;
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(s0), "=f"(s1) : "l"(sv));
-        asm("min.f32 %0, %1, %2, %3;" : "=f"(acc[r][c]) : "f"(acc[r][c]), "f"(s0), "f"(s1));
-      }
+      for (int c = 0; c < 8; ++c) s = fminf(s, acc[r][c]);
+    static_cast<float *>(sinkv)[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  } else {
+    int32_t s = 1 << 30;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) s = min(s, iacc[r][c]);
+    static_cast<int32_t *>(sinkv)[blockIdx.x * blockDim.x + threadIdx.x] = s;
   }
-  float s = 1e30f;
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) s = fminf(s, acc[r][c]);
-  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 }  // namespace
 
 extern "C" int apsp_ubench_minplus(int form, int64_t iters, int blocks, int threads, void *sink, void *stream,
                                    double *relax_per_s) {
-  if (!sink || !relax_per_s || iters <= 0 || threads <= 0 || threads > 1024 || form < 0 || form > 4)
-    return APSP_EINVAL;
+  if (!sink || !relax_per_s || iters <= 0 || form < 0 || form > 5) return APSP_EINVAL;
+  if (threads != 256) return APSP_EINVAL;  // the micro-tile layout is fixed
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (blocks <= 0) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return APSP_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return APSP_ECUDA;
-    blocks = 4 * sms;
+    blocks = 2 * sms;
   }
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return APSP_ECUDA;
+  if (cudaEventCreate(&e0) != cudaSuccess) return APSP_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return APSP_ECUDA;
+  }
   auto launch = [&](int64_t its) {
     switch (form) {
-      case 0: ubench_kernel<int32_t, 0><<<blocks, threads, 0, st>>>(its, (int32_t *)sink); break;
-      case 1: ubench_kernel<float, 1><<<blocks, threads, 0, st>>>(its, (float *)sink); break;
-      case 2: ubench_kernel<uint32_t, 2><<<blocks, threads, 0, st>>>(its, (uint32_t *)sink); break;
-      case 3: ubench_kernel<int32_t, 3><<<blocks, threads, 0, st>>>(its, (int32_t *)sink); break;
-      case 4: ubench_f32x2<<<blocks, threads, 0, st>>>(its, (float *)sink); break;
+      case 0: ubench_kstep<int32_t, 0><<<blocks, 256, 0, st>>>(its, (int32_t *)sink); break;
+      case 1: ubench_kstep<float, 1><<<blocks, 256, 0, st>>>(its, (float *)sink); break;
+      case 2: ubench_kstep<uint32_t, 2><<<blocks, 256, 0, st>>>(its, (uint32_t *)sink); break;
+      case 3: ubench_kstep<int32_t, 3><<<blocks, 256, 0, st>>>(its, (int32_t *)sink); break;
+      case 4: ubench_kpair<4><<<blocks, 256, 0, st>>>(its, sink); break;
+      case 5: ubench_kpair<5><<<blocks, 256, 0, st>>>(its, sink); break;
     }
   };
   launch(iters / 8 + 1);  // warm-up (clocks, instruction cache)
@@ -142,11 +209,14 @@ extern "C" int apsp_ubench_minplus(int form, int64_t iters, int blocks, int thre
   cudaEventRecord(e1, st);
   int rc = APSP_OK;
   float ms = 0.f;
-  if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = APSP_ECUDA;
+  if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+    rc = APSP_ECUDA;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != APSP_OK) return rc;
-  const double per_lane = (form == 2 || form == 4) ? 128.0 : 64.0;  // relaxations per iteration per thread
-  *relax_per_s = (double)blocks * threads * per_lane * (double)iters / (ms * 1e-3);
+  // relaxations per thread per sweep of the 32-k slice (int16x2: two per lane)
+  const double per_sweep = (form == 2 ? 2.0 : 1.0) * 64.0 * kKs;
+  *relax_per_s = (double)blocks * 256.0 * per_sweep * (double)iters / (ms * 1e-3);
   return APSP_OK;
 }

@@ -103,6 +103,31 @@ def test_phase3_order_independence(dt):
         assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("n,kb", [(700, 64), (1000, 128), (2048, 128)])
+def test_fp32_packed_equals_unpacked(n, kb):
+    # packed f32x2 + min3 phase 3 (workspace) vs one-k-at-a-time phase 3
+    w = inputs.dense_f32(n, seed=n)
+    a = gpu_solve(w, kblock=kb)
+    b = gpu_solve(w, kblock=kb, flags=binding.FLAG_NO_WORKSPACE)
+    c = gpu_solve(w, kblock=kb, flags=binding.FLAG_GENERIC)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_fp32_user_workspace():
+    n = 900
+    w, _ = inputs.dense_f32(n, seed=5, reweighted=True)
+    nbytes = binding.workspace_bytes(n, binding.APSP_F32)
+    assert nbytes == 64 * 960 * 4
+    ws = torch.full((nbytes // 4,), float("nan"), device="cuda")
+    t = torch.from_numpy(w).cuda()
+    binding.apsp_fw(t, workspace=ws)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(t.cpu().numpy(), gpu_solve(w, flags=binding.FLAG_NO_WORKSPACE))
+    small = torch.empty(nbytes // 4 - 1, device="cuda")
+    opt = binding.Options(0, 0, None, 0, small.data_ptr(), small.numel() * 4)
+    assert binding.apsp_fw_raw(t.data_ptr(), n, n, binding.APSP_F32, None, opt) == binding.APSP_EINVAL
+
+
 def test_graph_replay_same_buffer():
     w = inputs.c1(seed=4, n=520)
     exp = oracle.fw_int32_conv(w)
