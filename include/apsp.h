@@ -158,6 +158,27 @@ APSP_API int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, voi
  */
 APSP_API int64_t apsp_workspace_bytes(int64_t n, int dtype, int32_t kblock);
 
+/*
+ * apsp_fw for APSP_F32 that allocates nothing (the paper has no counterpart:
+ * this serves callers that may not allocate device memory on the solve path,
+ * e.g. a plugin whose host framework owns all device memory through its own
+ * pool, or a latency-critical service that cannot absorb cudaMalloc/cudaFree,
+ * which can fail mid-request and, for cudaFree, synchronize the device).
+ *   dist, n, ld, stream  as in apsp_fw (fp32 matrix, in place; the caller
+ *                        still owns and passes the matrix).
+ * The scratch the packed phase 3 needs (the interleaved row panel) lives in a
+ * static device array of the library, 8 MiB, held by every GPU that loads the
+ * library until the process exits.  Limit: n <= 16384; larger n returns
+ * APSP_EUNSUPPORTED before any device work.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the one array and each
+ * solve rewrites every part of it that it reads, so nothing needs clearing;
+ * calls whose work overlaps on the GPU (e.g. on two streams at once) race on
+ * it and must be serialized by the caller.  Launches kernels directly (no
+ * library-owned graph, stream or workspace).  Stream-ordered like apsp_fw.
+ */
+APSP_API int apsp_fw_f32_noalloc(void *dist, int64_t n, int64_t ld, void *stream);
+
 /* Fills *cfg with the configuration apsp_fw would use (no device work). */
 APSP_API int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_config *cfg);
 

@@ -24,7 +24,8 @@ INF_I16 = 16383
 
 # Every symbol include/apsp.h declares (checked by the tests).
 EXPORTS = ["apsp_status_str", "apsp_version", "apsp_fw", "apsp_fw_ex", "apsp_fw_host",
-           "apsp_workspace_bytes", "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus"]
+           "apsp_workspace_bytes", "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus",
+           "apsp_fw_f32_noalloc"]
 
 
 class Options(ctypes.Structure):
@@ -73,6 +74,7 @@ def lib() -> ctypes.CDLL:
             L.apsp_fw.argtypes = [vp, i64, i64, i32, vp]
             L.apsp_fw_ex.argtypes = [vp, i64, i64, i32, ctypes.POINTER(Options), vp]
             L.apsp_fw_host.argtypes = [vp, i64, i64, i32, vp]
+            L.apsp_fw_f32_noalloc.argtypes = [vp, i64, i64, vp]
             L.apsp_query_config.argtypes = [i64, i32, ctypes.c_int32, ctypes.POINTER(Config)]
             L.apsp_workspace_bytes.argtypes = [i64, i32, ctypes.c_int32]
             L.apsp_workspace_bytes.restype = i64

@@ -240,6 +240,10 @@ struct HostStage {
 HostStage g_host_stage[kMaxDev];
 
 }  // namespace
+
+int default_kblock(int64_t n, int dtype) { return choose_kblock(n, dtype, 0); }
+int error_word(int **err) { return device_words(err, nullptr); }
+
 }  // namespace apsp
 
 using namespace apsp;

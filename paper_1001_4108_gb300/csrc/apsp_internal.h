@@ -33,6 +33,12 @@ int run_i32(const RunArgs &a);
 int run_f32(const RunArgs &a);
 int run_i16(const RunArgs &a);
 
+// Tile side the C ABI picks for (n, dtype) when none is requested.
+int default_kblock(int64_t n, int dtype);
+// Device address of the device error word of the current device (set-up once
+// per device, no allocation).  Returns an apsp_status.
+int error_word(int **err);
+
 // cuTensorMapEncodeTiled from the driver, resolved once (nullptr if absent).
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
