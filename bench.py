@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--dtype", default="f32", choices=["f32", "i32"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "i32", "i16"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--kblock", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -55,9 +55,15 @@ def _dist_env():
     return rank, world, local
 
 
+def _i16_wmax(n):
+    return max(1, 16382 // max(n - 1, 1))  # (n - 1) * Wmax < 16383
+
+
 def _workload_name(dtype, n):
     if dtype == "f32":
         return f"dense complete directed graph, fp32 weights uniform in (0,1], n={n}"
+    if dtype == "i16":
+        return f"directed graph, edge probability 0.1, int16 weights uniform in [1,{_i16_wmax(n)}], n={n}"
     return f"directed graph, edge probability 0.3, int32 weights uniform in [1,1000], n={n}"
 
 
@@ -65,6 +71,8 @@ def _make_input(dtype, n, seed):
     from paper_1001_4108_gb300 import inputs
     if dtype == "f32":
         return inputs.dense_f32(n, seed=seed)
+    if dtype == "i16":
+        return inputs.to_int16(inputs.int_graph(n, 0.1, 1, _i16_wmax(n), seed=seed))
     return inputs.int_graph(n, 0.3, 1, 1000, seed=seed)
 
 
@@ -160,6 +168,8 @@ def cpu_baseline(dtype: str, n_sample: int = 2048):
     t0 = time.perf_counter()
     if dtype == "f32":
         oracle.fw_f64(w)
+    elif dtype == "i16":
+        oracle.fw_int16_conv(w)
     else:
         oracle.fw_int32_conv(w)
     dt = time.perf_counter() - t0
@@ -177,7 +187,7 @@ def run_reference(a):
     oracle.build()
     n_sample = 1024
     w = _make_input(a.dtype, n_sample, seed=0)
-    f = oracle.fw_f64 if a.dtype == "f32" else oracle.fw_int32_conv
+    f = {"f32": oracle.fw_f64, "i32": oracle.fw_int32_conv, "i16": oracle.fw_int16_conv}[a.dtype]
     for _ in range(a.warmup):
         f(w)
     t0 = time.perf_counter()
@@ -190,7 +200,7 @@ def run_reference(a):
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if a.dtype == "f32" else "int64", "data": "synthetic",
-        "config": {"workload": _workload_name(a.dtype, a.n), "sample_n": n_sample},
+        "config": {"workload": _workload_name(a.dtype, n_sample), "sample_n": n_sample},
         "cpu_baseline": {"value": value, "unit": "relaxations/s", "cores": 1, "kind": "oracle",
                          "sample": f"Fig. 1 triple loop, single thread, n={n_sample} per step"},
         "e2e": {"value": value, "unit": "relaxations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -212,8 +222,9 @@ def run_ours(a):
     build.build()
     L = binding.lib()
     n = a.n
-    es = 4
-    cfg = binding.query_config(n, binding.APSP_F32 if a.dtype == "f32" else binding.APSP_I32, a.kblock)
+    es = 2 if a.dtype == "i16" else 4
+    dcode = {"f32": binding.APSP_F32, "i32": binding.APSP_I32, "i16": binding.APSP_I16}[a.dtype]
+    cfg = binding.query_config(n, dcode, a.kblock)
     R = cfg.rounds
     w = _make_input(a.dtype, n, seed=rank)
     pristine = torch.from_numpy(w).cuda()
@@ -300,12 +311,12 @@ def run_ours(a):
     # SM sub-partition, 64 per SM per clock.  int32: one DPX add-min per
     # relaxation -> 64 relaxations/clock/SM.  fp32: one three-input min folds
     # two candidates (after one packed f32x2 add) -> 128 relaxations/clock/SM.
-    lanes = 128 if a.dtype == "f32" else 64
+    lanes = 64 if a.dtype == "i32" else 128  # int16x2: two relaxations per DPX lane
     peak = sms * sm_max * 1e6 * lanes
     # the same instruction form in isolation (phase-3 inner loop on shared-
     # memory operands, every SM): the sustained ceiling of the form
     sink = torch.empty(sms * 2 * 256, dtype=torch.int32, device="cuda")
-    form_ceiling = binding.ubench(4 if a.dtype == "f32" else 0, 2000, sink)
+    form_ceiling = binding.ubench({"f32": 4, "i32": 0, "i16": 2}[a.dtype], 2000, sink)
     p3_relax = float(cfg.phase3_relax_per_round)
     p3_mean_s = statistics.mean(p3_ms) * 1e-3 if p3_ms else float("nan")
     achieved = p3_relax / p3_mean_s
@@ -320,11 +331,13 @@ def run_ours(a):
                    "l2": "inputs larger than L2 (matrix %.2f GiB)" % (n * n * es / 2 ** 30),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu",
-                     "kernel": "fw_phase3_f32x2" if a.dtype == "f32" else "fw_tile_tma<int,128,0>",
+                     "kernel": {"f32": "fw_phase3_f32x2", "i32": "fw_tile_tma<int,S,0>",
+                                "i16": "fw_tile_s16x2<S,0>"}[a.dtype],
                      "achieved": achieved, "peak": peak,
                      "unit": "relaxations/s", "frac": achieved / peak,
                      "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz ({peak_kind} max clock) x {lanes} relaxations "
-                                   "per clock per SM (64 ALU-pipe lanes; fp32: 2 per three-input min)",
+                                   "per clock per SM (64 ALU-pipe lanes; fp32: 2 per three-input min; "
+                                   "int16x2: 2 per DPX lane)",
                      "form_ceiling": form_ceiling, "frac_of_form_ceiling": achieved / form_ceiling,
                      "traffic": _measured_traffic(a.dtype, n, cfg.kblock),
                      "traffic_source": "ncu dram__bytes_read+write of the same kernel at n=8192, scaled by tile count",

@@ -151,10 +151,11 @@ APSP_API int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, voi
 
 /*
  * Device workspace (bytes) a solve of this size uses; 0 if none.  fp32 solves
- * keep a k-pair-interleaved copy of the current pivot row panel there
- * (s * ceil(n/s) * s * 4 bytes, e.g. 8 MiB at n = 16384, s = 128), written by
- * phase 2 and read by phase 3.  Without a workspace the same results come
- * from a slower phase-3 kernel.
+ * keep a k-pair-interleaved copy of the current pivot row panel there, int16
+ * solves a copy of the current pivot column panel with every entry duplicated
+ * into both halves of a 32-bit word; both are s * ceil(n/s) * s * 4 bytes
+ * (8 MiB at n = 16384, s = 128), written by phase 2 and read by phase 3.
+ * Without a workspace the same results come from slower phase-3 kernels.
  */
 APSP_API int64_t apsp_workspace_bytes(int64_t n, int dtype, int32_t kblock);
 

@@ -227,8 +227,10 @@ void *library_workspace(int dev, cudaStream_t stream, size_t bytes, bool capturi
 }
 
 size_t workspace_bytes_for(int64_t n, int dtype, int S) {
-  if (dtype != APSP_F32 || n <= S) return 0;
-  return interleaved_panel_bytes(n, S);
+  if (n <= S) return 0;
+  if (dtype == APSP_F32) return interleaved_panel_bytes(n, S);
+  if (dtype == APSP_I16) return replicated_panel_bytes(n, S);
+  return 0;
 }
 
 // Device buffer of apsp_fw_host, one per device, grown on demand.
@@ -276,8 +278,8 @@ extern "C" int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_conf
   const int S = choose_kblock(n, dtype, kblock);
   cfg->kblock = S;
   cfg->rounds = (int32_t)((n + S - 1) / S);
-  cfg->phase3_tma = dtype != APSP_I16 ? 1 : 0;
-  cfg->phase3_threads = cfg->phase3_tma ? (S / 8) * (S / 8) : 256;
+  cfg->phase3_tma = 1;
+  cfg->phase3_threads = (S / 8) * (S / 8);
   const int64_t m = std::max<int64_t>(n - S, 0);
   cfg->phase3_relax_per_round = m * m * S;
   return APSP_OK;
@@ -304,7 +306,7 @@ extern "C" int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const ap
   a.stream = static_cast<cudaStream_t>(stream);
   a.err = err;
   const size_t es = (size_t)elem_size(dtype);
-  a.tma_ok = dtype != APSP_I16 && (reinterpret_cast<uintptr_t>(dist) % 16 == 0) && ((size_t)ld * es) % 16 == 0;
+  a.tma_ok = (reinterpret_cast<uintptr_t>(dist) % 16 == 0) && ((size_t)ld * es) % 16 == 0;
 
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(a.stream, &cap) != cudaSuccess) return APSP_ECUDA;

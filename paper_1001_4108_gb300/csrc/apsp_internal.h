@@ -22,6 +22,13 @@ struct RunArgs {
   size_t ws_bytes;
 };
 
+// Workspace bytes of the packed int16x2 phase 3 (replicated column panel:
+// n_p rows x s words).
+inline size_t replicated_panel_bytes(int64_t n, int S) {
+  const int64_t np = (n + S - 1) / S * S;
+  return (size_t)np * (size_t)S * sizeof(uint32_t);
+}
+
 // Workspace bytes of the packed fp32 phase 3 (interleaved row panel).
 inline size_t interleaved_panel_bytes(int64_t n, int S) {
   const int64_t np = (n + S - 1) / S * S;

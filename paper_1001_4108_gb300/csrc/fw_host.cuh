@@ -14,6 +14,35 @@ template <typename T> struct TmaType;
 template <> struct TmaType<int32_t> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_INT32; };
 template <> struct TmaType<float> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; };
 
+// Tensor maps of the packed int16x2 path: the int16 matrix for the A box
+// (32 k's x S rows) and the B box (S columns x 32 k's), and the replicated
+// column panel in the workspace (S words x n_p rows, 128-byte swizzle).
+template <int S>
+static bool make_s16_maps(int16_t *d, int64_t n, int64_t ld, uint32_t *arep, int64_t np, CUtensorMap *mA16,
+                          CUtensorMap *mB16, CUtensorMap *mArep) {
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return false;
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(int16_t)};
+  const cuuint32_t boxA[2] = {(cuuint32_t)P3S16<S>::KS, (cuuint32_t)S};
+  const cuuint32_t boxB[2] = {(cuuint32_t)S, (cuuint32_t)P3S16<S>::KS};
+  if (enc(mA16, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, d, dims, strides, boxA, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  if (enc(mB16, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, d, dims, strides, boxB, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const cuuint64_t rdims[2] = {(cuuint64_t)S, (cuuint64_t)np};
+  const cuuint64_t rstr[1] = {(cuuint64_t)S * sizeof(uint32_t)};
+  const cuuint32_t rbox[2] = {(cuuint32_t)P3S16<S>::KS, (cuuint32_t)S};
+  return enc(mArep, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, arep, rdims, rstr, rbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tensor maps of the matrix for the two panel boxes of phase 3.
 template <typename T, int S>
 static bool make_panel_maps(T *d, int64_t n, int64_t ld, CUtensorMap *mA, CUtensorMap *mB) {
@@ -92,6 +121,12 @@ static int run_rounds(const RunArgs &a) {
           return APSP_ECUDA;
       }
     }
+    if constexpr (std::is_same<T, int16_t>::value) {
+      const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+      if (cudaFuncSetAttribute(fw_tile_s16x2<S, 0>, attr, P3S16<S>::SMEM) != cudaSuccess ||
+          cudaFuncSetAttribute(fw_tile_s16x2<S, 1>, attr, P3S16<S>::SMEM) != cudaSuccess)
+        return APSP_ECUDA;
+    }
     setup_done_mask |= 1 << (dev & 31);
   }
 
@@ -116,6 +151,16 @@ static int run_rounds(const RunArgs &a) {
     }
   }
 
+  CUtensorMap mA16, mB16, mArep;
+  bool use_s16 = false;
+  uint32_t *arep = nullptr;
+  if constexpr (std::is_same<T, int16_t>::value) {
+    arep = static_cast<uint32_t *>(a.ws);
+    use_s16 = a.tma_ok && !generic_only && R > 1 && a.ws && a.ws_bytes >= replicated_panel_bytes(n, S) &&
+              reinterpret_cast<uintptr_t>(a.ws) % 256 == 0 &&
+              make_s16_maps<S>(reinterpret_cast<int16_t *>(d), n, ld, arep, np, &mA16, &mB16, &mArep);
+  }
+
   auto ev = [&](int64_t idx) -> bool {
     if (!a.events || idx >= a.n_events) return true;
     return cudaEventRecord(static_cast<cudaEvent_t>(a.events[idx]), st) == cudaSuccess;
@@ -130,6 +175,13 @@ static int run_rounds(const RunArgs &a) {
     T *bp_round = (use_packed && full_k) ? bp : nullptr;
     if (R > 1) {
       bool launched2 = false;
+      if constexpr (std::is_same<T, int16_t>::value) {
+        if (use_s16 && full_k) {
+          fw_tile_s16x2<S, 1><<<2 * (R - 1), P3S16<S>::TPB, P3S16<S>::SMEM, st>>>(
+              mA16, mB16, reinterpret_cast<int16_t *>(d), n, ld, b, R, reverse, arep, a.err);
+          launched2 = true;
+        }
+      }
       if constexpr (HAS_TMA) {
         if (use_tma && full_k) {
           fw_tile_tma<T, S, 1><<<2 * (R - 1), P3Tma<S>::TPB, P3Tma<S>::SMEM, st>>>(
@@ -144,6 +196,13 @@ static int run_rounds(const RunArgs &a) {
     if (R > 1) {
       const dim3 grid(R - 1, R - 1);
       bool launched = false;
+      if constexpr (std::is_same<T, int16_t>::value) {
+        if (use_s16 && full_k) {
+          fw_tile_s16x2<S, 0><<<grid, P3S16<S>::TPB, P3S16<S>::SMEM, st>>>(
+              mArep, mB16, reinterpret_cast<int16_t *>(d), n, ld, b, R, reverse, arep, a.err);
+          launched = true;
+        }
+      }
       if constexpr (std::is_same<T, float>::value) {
         if (bp_round) {
           // interior tiles (all rows/columns inside the matrix), then the

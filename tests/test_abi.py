@@ -69,6 +69,6 @@ def test_query_config(L):
     c = binding.query_config(1000, binding.APSP_I32)
     assert c.kblock == 64 and c.rounds == 16
     c = binding.query_config(1000, binding.APSP_I16, 128)
-    assert c.kblock == 128 and c.rounds == 8 and c.phase3_tma == 0
+    assert c.kblock == 128 and c.rounds == 8 and c.phase3_tma == 1
     cfg = binding.Config()
     assert L.apsp_query_config(10, 1, 100, ctypes.byref(cfg)) == binding.APSP_EINVAL

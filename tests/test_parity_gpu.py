@@ -205,6 +205,32 @@ def test_c3_int16_exact(n):
     np.testing.assert_array_equal(np.where(d16 == inputs.INF_I16, INF, d16.astype(np.int32)), d32)
 
 
+@pytest.mark.parametrize("n,ld,kb", [(700, 704, 64), (1000, 1000, 128), (1030, 1032, 128), (2048, 2048, 128)])
+def test_int16_packed_vs_generic_vs_oracle(n, ld, kb):
+    # packed int16x2 DPX phases 2-3 (workspace) against the scalar kernels and the oracle
+    w32 = inputs.int_graph(n, 0.1, 1, 7, seed=n + 3)
+    w16 = np.full((n, ld), 5, np.int16)
+    w16[:, :n] = inputs.to_int16(w32)
+    a = gpu_solve(w16, n, kblock=kb)
+    b = gpu_solve(w16, n, kblock=kb, flags=binding.FLAG_GENERIC)
+    c = gpu_solve(w16, n, kblock=kb, flags=binding.FLAG_REVERSE_K)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+    np.testing.assert_array_equal(a[:, :n], oracle.fw_int16_conv(np.ascontiguousarray(w16[:, :n])))
+    assert (a[:, n:] == 5).all()
+
+
+def test_int16_large_vs_int32_and_dijkstra():
+    n = 4096
+    w32 = inputs.int_graph(n, 0.1, 1, 3, seed=41)
+    w16 = inputs.to_int16(w32)
+    d16 = gpu_solve(w16)
+    d32 = gpu_solve(w32)
+    np.testing.assert_array_equal(np.where(d16 == inputs.INF_I16, INF, d16.astype(np.int32)), d32)
+    rows = [0, 1234, 4095]
+    np.testing.assert_array_equal(d32[rows], oracle.dijkstra_rows_i32(w32, rows))
+
+
 # --------------------------------------------------------------- host path ---
 
 def test_host_entry_point():
