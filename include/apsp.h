@@ -137,6 +137,23 @@ APSP_API int apsp_version(void);
  */
 APSP_API int apsp_fw(void *dist, int64_t n, int64_t ld, int dtype, void *stream);
 
+/*
+ * Many independent graphs in one call (e.g. thousands of small graphs).
+ *   dists  host array of `count` device pointers (matrices in place);
+ *   ns, lds host arrays of vertex counts and leading dimensions;
+ *   dtype  one element type for all graphs.
+ * The arrays are read before the call returns (the caller keeps ownership).
+ * Graphs with n <= 512 are solved by one persistent launch in which each CTA
+ * takes a graph (largest first) and runs all stages of Fig. 2 for it; larger
+ * graphs use the apsp_fw path.  Solving the same batch (same matrices and
+ * stream) again replays a CUDA graph of that launch.  Not allowed while the
+ * stream is being captured (APSP_EUNSUPPORTED).  Results equal apsp_fw's for
+ * integers; for fp32 they agree within the rounding of the additions.
+ * Returns the first argument error (before any work) or APSP_ECUDA.
+ */
+APSP_API int apsp_fw_batched(void *const *dists, const int64_t *ns, const int64_t *lds, int64_t count, int dtype,
+                             void *stream);
+
 /* apsp_fw with options (NULL = defaults).  See apsp_options. */
 APSP_API int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt,
                void *stream);

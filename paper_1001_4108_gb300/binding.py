@@ -25,7 +25,7 @@ INF_I16 = 16383
 # Every symbol include/apsp.h declares (checked by the tests).
 EXPORTS = ["apsp_status_str", "apsp_version", "apsp_fw", "apsp_fw_ex", "apsp_fw_host",
            "apsp_workspace_bytes", "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus",
-           "apsp_fw_f32_noalloc"]
+           "apsp_fw_f32_noalloc", "apsp_fw_batched"]
 
 
 class Options(ctypes.Structure):
@@ -75,6 +75,8 @@ def lib() -> ctypes.CDLL:
             L.apsp_fw_ex.argtypes = [vp, i64, i64, i32, ctypes.POINTER(Options), vp]
             L.apsp_fw_host.argtypes = [vp, i64, i64, i32, vp]
             L.apsp_fw_f32_noalloc.argtypes = [vp, i64, i64, vp]
+            L.apsp_fw_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64), i64, i32, vp]
             L.apsp_query_config.argtypes = [i64, i32, ctypes.c_int32, ctypes.POINTER(Config)]
             L.apsp_workspace_bytes.argtypes = [i64, i32, ctypes.c_int32]
             L.apsp_workspace_bytes.restype = i64
@@ -114,8 +116,11 @@ def _stream_handle(stream) -> int | None:
 def _matrix_args(d, n):
     """(ptr, n, ld, dtype) of a 2-D CUDA tensor whose leading n x n block is
     the matrix (row stride = ld, unit column stride)."""
-    assert d.dim() == 2 and d.stride(1) == 1, "row-major matrix with unit column stride expected"
+    assert d.dim() == 2, "2-D matrix expected"
     n = d.shape[0] if n is None else n
+    if n == 0:
+        return d.data_ptr(), 0, 0, dtype_code(d.dtype)
+    assert d.stride(1) == 1, "row-major matrix with unit column stride expected"
     assert d.shape[0] >= n and d.shape[1] >= n
     return d.data_ptr(), n, d.stride(0), dtype_code(d.dtype)
 
@@ -142,6 +147,24 @@ def apsp_fw(d, n: int | None = None, *, kblock: int = 0, flags: int = 0, events=
         opt.n_events = len(events)
     _check(lib().apsp_fw_ex(ptr, n, ld, dt, ctypes.byref(opt), s), "apsp_fw_ex")
     return d
+
+
+def apsp_fw_batched(mats, stream=None, ns=None):
+    """Many graphs in one call: ``mats`` is a list of 2-D CUDA tensors of one
+    dtype (each solved in place on its leading n x n block)."""
+    if not mats:
+        return mats
+    ptrs, nn, lds, dts = [], [], [], set()
+    for i, m in enumerate(mats):
+        p, n, ld, dt = _matrix_args(m, None if ns is None else ns[i])
+        ptrs.append(p); nn.append(n); lds.append(ld); dts.add(dt)
+    assert len(dts) == 1, "one dtype per batch"
+    cnt = len(mats)
+    P = (ctypes.c_void_p * cnt)(*ptrs)
+    N = (ctypes.c_int64 * cnt)(*nn)
+    LD = (ctypes.c_int64 * cnt)(*lds)
+    _check(lib().apsp_fw_batched(P, N, LD, cnt, dts.pop(), _stream_handle(stream)), "apsp_fw_batched")
+    return mats
 
 
 def apsp_fw_raw(ptr: int, n: int, ld: int, dtype: int, stream: int | None, opt: Options | None = None) -> int:

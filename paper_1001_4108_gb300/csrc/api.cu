@@ -332,6 +332,36 @@ extern "C" int apsp_fw(void *dist, int64_t n, int64_t ld, int dtype, void *strea
   return apsp_fw_ex(dist, n, ld, dtype, nullptr, stream);
 }
 
+extern "C" int apsp_fw_batched(void *const *dists, const int64_t *ns, const int64_t *lds, int64_t count, int dtype,
+                               void *stream) {
+  if (count < 0 || (count > 0 && (!dists || !ns || !lds))) return APSP_EINVAL;
+  if (count > (int64_t)1 << 30) return APSP_EUNSUPPORTED;
+  for (int64_t g = 0; g < count; ++g) {
+    const int st = check_args(dists[g], ns[g], lds[g], dtype, nullptr);
+    if (st != APSP_OK) return st;
+  }
+  if (count == 0) return APSP_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= kMaxDev) return APSP_ECUDA;
+  // largest first: the persistent CTAs finish together
+  std::vector<int64_t> order((size_t)count);
+  for (int64_t g = 0; g < count; ++g) order[(size_t)g] = g;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ns[x] > ns[y]; });
+  std::vector<BatchDesc> small;
+  small.reserve((size_t)count);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int64_t g : order) {
+    if (ns[g] == 0) continue;
+    if (ns[g] > kBatchCtaMaxN) {
+      const int st = apsp_fw_ex(dists[g], ns[g], lds[g], dtype, nullptr, stream);
+      if (st != APSP_OK) return st;
+    } else {
+      small.push_back({dists[g], lds[g], ns[g]});
+    }
+  }
+  return run_batched_small(small.data(), (int)small.size(), dtype, s, dev);
+}
+
 extern "C" int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, void *stream) {
   int st = check_args(host_dist, n, ld, dtype, nullptr);
   if (st != APSP_OK) return st;

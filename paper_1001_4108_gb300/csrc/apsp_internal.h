@@ -35,6 +35,19 @@ inline size_t interleaved_panel_bytes(int64_t n, int S) {
   return (size_t)S * (size_t)np * sizeof(float);
 }
 
+// One graph of a batch (device matrix, leading dimension, vertices).
+struct BatchDesc {
+  void *d;
+  int64_t ld;
+  int64_t n;
+};
+// Largest n the one-CTA-per-graph batched kernel takes; larger graphs of a
+// batch go through the multi-CTA path.
+constexpr int64_t kBatchCtaMaxN = 512;
+// Solves graphs (all n <= kBatchCtaMaxN, sorted largest first) with the
+// persistent batched kernel.  Returns an apsp_status.
+int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStream_t st, int dev);
+
 // Enqueue every stage of Fig. 2 for one matrix.  Returns an apsp_status.
 int run_i32(const RunArgs &a);
 int run_f32(const RunArgs &a);

@@ -72,3 +72,14 @@ def test_query_config(L):
     assert c.kblock == 128 and c.rounds == 8 and c.phase3_tma == 1
     cfg = binding.Config()
     assert L.apsp_query_config(10, 1, 100, ctypes.byref(cfg)) == binding.APSP_EINVAL
+
+
+def test_batched_bad_arguments(L):
+    import ctypes as C
+    P = (C.c_void_p * 2)(0x1000, 0)
+    N = (C.c_int64 * 2)(4, 4)
+    LD = (C.c_int64 * 2)(4, 4)
+    # second matrix is null with n > 0
+    assert L.apsp_fw_batched(P, N, LD, 2, binding.APSP_I32, None) == binding.APSP_EINVAL
+    assert L.apsp_fw_batched(P, N, LD, -1, binding.APSP_I32, None) == binding.APSP_EINVAL
+    assert L.apsp_fw_batched(None, None, None, 0, binding.APSP_I32, None) == binding.APSP_OK

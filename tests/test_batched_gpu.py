@@ -1,0 +1,94 @@
+"""Batched form (apsp_fw_batched): many graphs of uneven n in one persistent
+launch.  Integer results must be bit-identical to the oracle and to one
+apsp_fw call per graph; fp32 within the parity tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1001_4108_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+INF = inputs.INF_I32
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    binding.lib()
+    yield
+    assert binding.device_error() == 0
+
+
+def _to_gpu(ws):
+    return [torch.from_numpy(np.ascontiguousarray(w)).cuda() for w in ws]
+
+
+def test_c4_small_batch_vs_oracle():
+    ws = inputs.c4_batch(48, seed=7)
+    ts = _to_gpu(ws)
+    binding.apsp_fw_batched(ts)
+    torch.cuda.synchronize()
+    for w, t in zip(ws, ts):
+        np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
+
+
+def test_c4_full_batch_equals_per_graph_launches():
+    ws = inputs.c4_batch(4096, seed=8)
+    a = _to_gpu(ws)
+    b = _to_gpu(ws)
+    binding.apsp_fw_batched(a)
+    for t in b:
+        binding.apsp_fw(t)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    # replay (second call of the same batch runs its CUDA graph)
+    c = _to_gpu(ws[:300])
+    for _ in range(3):
+        for t, w in zip(c, ws[:300]):
+            t.copy_(torch.from_numpy(w))
+        binding.apsp_fw_batched(c)
+        torch.cuda.synchronize()
+        for x, y in zip(c, b[:300]):
+            assert torch.equal(x, y)
+
+
+def test_mixed_sizes_and_dtypes():
+    g = inputs.rng(9)
+    ns = [0, 1, 2, 63, 64, 65, 200, 511, 512, 513, 700]
+    ws = [inputs.int_graph(n, 0.2, 0, 1000, seed=int(g.integers(1 << 30)), potential_max=40) for n in ns]
+    ts = _to_gpu(ws)
+    binding.apsp_fw_batched(ts)
+    torch.cuda.synchronize()
+    for w, t in zip(ws, ts):
+        np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
+    # fp32 (reweighted, negative edges) within tolerance
+    fs = [inputs.dense_f32(n, seed=n, reweighted=True) for n in (17, 130, 300)]
+    tf = _to_gpu([w for w, _ in fs])
+    binding.apsp_fw_batched(tf)
+    torch.cuda.synchronize()
+    for (w, pot), t in zip(fs, tf):
+        d64 = oracle.fw_f64(w)
+        d0 = d64 - pot[:, None] + pot[None, :]
+        err = np.abs(t.cpu().numpy().astype(np.float64) - d64)
+        assert (err <= 1e-5 * np.maximum(np.abs(d64), np.abs(d0) + 2 * pot.max())).all()
+    # int16
+    hs = [inputs.c3(seed=n, n=n)[1] for n in (40, 256, 400)]
+    th = _to_gpu(hs)
+    binding.apsp_fw_batched(th)
+    torch.cuda.synchronize()
+    for w, t in zip(hs, th):
+        np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int16_conv(w))
+
+
+def test_batched_padded_leading_dimension():
+    ws = [inputs.int_graph(n, 0.3, 1, 100, seed=n, ld=n + 5) for n in (50, 129, 333)]
+    ts = _to_gpu(ws)
+    binding.apsp_fw_batched(ts, ns=[50, 129, 333])
+    torch.cuda.synchronize()
+    for w, t, n in zip(ws, ts, (50, 129, 333)):
+        out = t.cpu().numpy()
+        np.testing.assert_array_equal(out[:, :n], oracle.fw_int32_conv(np.ascontiguousarray(w[:, :n])))
+        assert (out[:, n:] == -7).all()
