@@ -197,6 +197,27 @@ APSP_API int64_t apsp_workspace_bytes(int64_t n, int dtype, int32_t kblock);
  */
 APSP_API int apsp_fw_f32_noalloc(void *dist, int64_t n, int64_t ld, void *stream);
 
+/*
+ * Autotuner (the paper has none; in the spirit of the per-architecture code
+ * generator it cites).  Times, on this GPU and for one element type:
+ *   - the batched kernel shapes (tile side 32/64/128, 2x2 or 4x4 register
+ *     block per thread) on synthetic batches for n buckets <= 32, 64, 128,
+ *     256, 512, keeping the fastest shape per bucket;
+ *   - the single-graph k-block depth (64 vs 128) at n = 1024 ... 6144,
+ *     keeping the smallest n from which 128 stays faster.
+ * The choices replace the built-in defaults for later calls in this process
+ * (apsp_fw with kblock 0, apsp_fw_batched).  Allocates and frees its own test
+ * matrices; synchronizes the stream; takes seconds.  If report != NULL, a JSON
+ * summary of the timings is written there (truncated to report_len - 1 chars).
+ */
+APSP_API int apsp_autotune(int dtype, void *stream, char *report, int64_t report_len);
+
+/* Save / load the tuning table (all element types) as a small text file.
+   Load validates every entry and leaves the table unchanged on error
+   (APSP_EINVAL). */
+APSP_API int apsp_tuning_save(const char *path);
+APSP_API int apsp_tuning_load(const char *path);
+
 /* Fills *cfg with the configuration apsp_fw would use (no device work). */
 APSP_API int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_config *cfg);
 

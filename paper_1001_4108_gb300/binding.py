@@ -25,7 +25,8 @@ INF_I16 = 16383
 # Every symbol include/apsp.h declares (checked by the tests).
 EXPORTS = ["apsp_status_str", "apsp_version", "apsp_fw", "apsp_fw_ex", "apsp_fw_host",
            "apsp_workspace_bytes", "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus",
-           "apsp_fw_f32_noalloc", "apsp_fw_batched"]
+           "apsp_fw_f32_noalloc", "apsp_fw_batched", "apsp_autotune", "apsp_tuning_save",
+           "apsp_tuning_load"]
 
 
 class Options(ctypes.Structure):
@@ -75,6 +76,9 @@ def lib() -> ctypes.CDLL:
             L.apsp_fw_ex.argtypes = [vp, i64, i64, i32, ctypes.POINTER(Options), vp]
             L.apsp_fw_host.argtypes = [vp, i64, i64, i32, vp]
             L.apsp_fw_f32_noalloc.argtypes = [vp, i64, i64, vp]
+            L.apsp_autotune.argtypes = [i32, vp, ctypes.c_char_p, i64]
+            L.apsp_tuning_save.argtypes = [ctypes.c_char_p]
+            L.apsp_tuning_load.argtypes = [ctypes.c_char_p]
             L.apsp_fw_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64), i64, i32, vp]
             L.apsp_query_config.argtypes = [i64, i32, ctypes.c_int32, ctypes.POINTER(Config)]
@@ -191,6 +195,24 @@ def apsp_fw_host(a, stream=None):
 def workspace_bytes(n: int, dtype, kblock: int = 0) -> int:
     dt = dtype if isinstance(dtype, int) else dtype_code(dtype)
     return int(lib().apsp_workspace_bytes(n, dt, kblock))
+
+
+def autotune(dtype, stream=None) -> dict:
+    """Time the batched kernel shapes and the k-block crossover on this GPU and
+    use the winners from now on (see apsp_autotune).  Returns the report."""
+    import json
+    dt = dtype if isinstance(dtype, int) else dtype_code(dtype)
+    buf = ctypes.create_string_buffer(1 << 14)
+    _check(lib().apsp_autotune(dt, _stream_handle(stream), buf, len(buf)), "apsp_autotune")
+    return json.loads(buf.value.decode())
+
+
+def tuning_save(path: str):
+    _check(lib().apsp_tuning_save(path.encode()), "apsp_tuning_save")
+
+
+def tuning_load(path: str):
+    _check(lib().apsp_tuning_load(path.encode()), "apsp_tuning_load")
 
 
 def query_config(n: int, dtype, kblock: int = 0) -> Config:

@@ -58,11 +58,11 @@ int device_words(int **err, int **neg) {
 }
 
 // Tile side s: 64 keeps enough doubly dependent tiles in flight for small n,
-// 128 halves the HBM traffic per relaxation (2 * elem / s bytes) for large n.
+// 128 halves the HBM traffic per relaxation (2 * elem / s bytes) for large n;
+// the crossover comes from the tuning table (apsp_autotune).
 int choose_kblock(int64_t n, int dtype, int32_t requested) {
   if (requested == 64 || requested == 128) return requested;
-  (void)dtype;
-  return n < 4096 ? 64 : 128;
+  return tuned_kblock(n, dtype);
 }
 
 int check_args(const void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt) {

@@ -48,6 +48,15 @@ constexpr int64_t kBatchCtaMaxN = 512;
 // persistent batched kernel.  Returns an apsp_status.
 int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStream_t st, int dev);
 
+// Autotuned choices (defaults until apsp_autotune / apsp_tuning_load).
+// Batched kernel shapes: 0 = (s 32, 2x2), 1 = (s 32, 4x4), 2 = (s 64, 4x4),
+// 3 = (s 128, 4x4).
+constexpr int kBatchVariants = 4;
+int tuned_batch_variant(int64_t n, int dtype);
+int tuned_kblock(int64_t n, int dtype);
+int time_batched_variant(const BatchDesc *dev_descs, int count, int *counter, int dtype, int variant,
+                         cudaStream_t st, float *ms);
+
 // Enqueue every stage of Fig. 2 for one matrix.  Returns an apsp_status.
 int run_i32(const RunArgs &a);
 int run_f32(const RunArgs &a);

@@ -18,82 +18,91 @@ namespace apsp {
 
 namespace {
 
-constexpr int kBS = 64;          // tile side = k-block depth inside a CTA
-constexpr int kBLD = kBS + 4;    // padded shared-memory row stride
-constexpr int kBThreads = 256;   // (kBS / 4)^2: a 4 x 4 register block per thread
-constexpr size_t kBSmem = 3 * (size_t)kBS * kBLD * 4 + 4 * kBS * 4 + 16;
+// Kernel shape: tile side S (= k-block depth inside the CTA) and an M x M
+// register block per thread, (S/M)^2 threads; rows M*ty+a, columns M*tx+c.
+template <int S, int M> struct BShape {
+  static constexpr int Q = S / M;                 // threads per dimension
+  static constexpr int NT = Q * Q;
+  static constexpr int LD = S + 4;                // padded shared-memory row stride
+  static constexpr size_t SMEM = 3 * (size_t)S * LD * 4 + 4 * (size_t)S * 4 + 16;
+};
 
-template <typename T>
+template <typename T, int S, int M>
 struct TileIO {
   using C = typename Arith<T>::C;
-  // 4 x 4 block of tile (r0, c0) owned by (ty, tx): rows r0+4ty+a, cols c0+4tx+c
+  static constexpr int LD = BShape<S, M>::LD;
   __device__ static void load(const T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, int ty, int tx,
-                              C (&x)[4][4]) {
+                              C (&x)[M][M]) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < M; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int64_t gi = r0 + 4 * ty + a, gj = c0 + 4 * tx + c;
+      for (int c = 0; c < M; ++c) {
+        const int64_t gi = r0 + M * ty + a, gj = c0 + M * tx + c;
         x[a][c] = (gi < n && gj < n) ? Arith<T>::load(d[gi * ld + gj]) : Arith<T>::inf();
       }
   }
   __device__ static void store(T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, int ty, int tx,
-                               const C (&x)[4][4], bool last) {
+                               const C (&x)[M][M], bool last) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < M; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int64_t gi = r0 + 4 * ty + a, gj = c0 + 4 * tx + c;
+      for (int c = 0; c < M; ++c) {
+        const int64_t gi = r0 + M * ty + a, gj = c0 + M * tx + c;
         if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(x[a][c]) : (T)x[a][c];
       }
   }
-  __device__ static void to_smem(C *s, int ty, int tx, const C (&x)[4][4]) {
+  __device__ static void to_smem(C *s, int ty, int tx, const C (&x)[M][M]) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < M; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) s[(4 * ty + a) * kBLD + 4 * tx + c] = x[a][c];
+      for (int c = 0; c < M; ++c) s[(M * ty + a) * LD + M * tx + c] = x[a][c];
   }
 };
 
-// acc[a][c] <- min(acc[a][c], min_k A[4ty+a][k] + B[k][4tx+c]) over the tile's
-// k's; A and B row-major in shared memory with stride kBLD.
-template <typename T>
-__device__ __forceinline__ void minplus_tile(typename Arith<T>::C (&acc)[4][4], const typename Arith<T>::C *A,
+// acc[a][c] <- min(acc[a][c], min_k A[M ty + a][k] + B[k][M tx + c]) over the
+// tile's k's; A and B row-major in shared memory with the padded stride.
+template <typename T, int S, int M>
+__device__ __forceinline__ void minplus_tile(typename Arith<T>::C (&acc)[M][M], const typename Arith<T>::C *A,
                                              const typename Arith<T>::C *B, int ty, int tx) {
   using C = typename Arith<T>::C;
+  constexpr int LD = BShape<S, M>::LD;
 #pragma unroll 4
-  for (int kq = 0; kq < kBS / 4; ++kq) {
-    C av[4][4];
+  for (int kq = 0; kq < S / 4; ++kq) {
+    C av[M][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const C *p = A + (4 * ty + a) * kBLD + 4 * kq;
+    for (int a = 0; a < M; ++a) {
+      const C *p = A + (M * ty + a) * LD + 4 * kq;
       av[a][0] = p[0]; av[a][1] = p[1]; av[a][2] = p[2]; av[a][3] = p[3];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const C *q = B + (4 * kq + u) * kBLD + 4 * tx;
-      const C bv[4] = {q[0], q[1], q[2], q[3]};
+      const C *q = B + (4 * kq + u) * LD + M * tx;
+      C bv[M];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < M; ++c) bv[c] = q[c];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = Arith<T>::relax(acc[a][c], av[a][u], bv[c]);
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int c = 0; c < M; ++c) acc[a][c] = Arith<T>::relax(acc[a][c], av[a][u], bv[c]);
     }
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBThreads) fw_batched_cta(const BatchDesc *__restrict__ descs, int count,
-                                                            int *counter) {
+template <typename T, int S, int M>
+__global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDesc *__restrict__ descs, int count,
+                                                                   int *counter) {
   using C = typename Arith<T>::C;
-  using IO = TileIO<T>;
+  using IO = TileIO<T, S, M>;
+  constexpr int Q = BShape<S, M>::Q;
+  constexpr int LD = BShape<S, M>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *Ds = reinterpret_cast<C *>(smem_raw);  // closed diagonal tile
-  C *Ps = Ds + kBS * kBLD;                  // first operand tile
-  C *Qs = Ps + kBS * kBLD;                  // second operand tile
-  C *rowbuf = Qs + kBS * kBLD;              // [2][kBS]
-  C *colbuf = rowbuf + 2 * kBS;             // [2][kBS]
-  int *s_g = reinterpret_cast<int *>(colbuf + 2 * kBS);
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  C *Ps = Ds + S * LD;                      // first operand tile
+  C *Qs = Ps + S * LD;                      // second operand tile
+  C *rowbuf = Qs + S * LD;                  // [2][S]
+  C *colbuf = rowbuf + 2 * S;               // [2][S]
+  int *s_g = reinterpret_cast<int *>(colbuf + 2 * S);
+  const int tx = threadIdx.x % Q, ty = threadIdx.x / Q;
 
   while (true) {
     if (threadIdx.x == 0) *s_g = atomicAdd(counter, 1);
@@ -103,42 +112,42 @@ __global__ void __launch_bounds__(kBThreads) fw_batched_cta(const BatchDesc *__r
     if (g >= count) return;
     T *d = static_cast<T *>(descs[g].d);
     const int64_t n = descs[g].n, ld = descs[g].ld;
-    const int R = (int)((n + kBS - 1) / kBS);
+    const int R = (int)((n + S - 1) / S);
 
     for (int b = 0; b < R; ++b) {
       const bool last = b == R - 1;
-      const int64_t p0 = (int64_t)b * kBS;
+      const int64_t p0 = (int64_t)b * S;
       // ---- phase 1: close the diagonal tile (registers + row/column k broadcast)
-      C x[4][4];
+      C x[M][M];
       IO::load(d, ld, n, p0, p0, ty, tx, x);
       if (ty == 0)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) rowbuf[4 * tx + c] = x[0][c];
+        for (int c = 0; c < M; ++c) rowbuf[M * tx + c] = x[0][c];
       if (tx == 0)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) colbuf[4 * ty + a] = x[a][0];
-      for (int kq = 0; kq < kBS / 4; ++kq) {
+        for (int a = 0; a < M; ++a) colbuf[M * ty + a] = x[a][0];
+      for (int kq = 0; kq < Q; ++kq) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int k = 4 * kq + u;
+        for (int u = 0; u < M; ++u) {
+          const int k = M * kq + u;
           __syncthreads();
-          C rk[4], ck[4];
+          C rk[M], ck[M];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) rk[c] = rowbuf[(k & 1) * kBS + 4 * tx + c];
+          for (int c = 0; c < M; ++c) rk[c] = rowbuf[(k & 1) * S + M * tx + c];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) ck[a] = colbuf[(k & 1) * kBS + 4 * ty + a];
+          for (int a = 0; a < M; ++a) ck[a] = colbuf[(k & 1) * S + M * ty + a];
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+          for (int a = 0; a < M; ++a)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) x[a][c] = Arith<T>::relax(x[a][c], ck[a], rk[c]);
+            for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::relax(x[a][c], ck[a], rk[c]);
           const int k1 = k + 1;
-          if (k1 < kBS) {
-            if (ty == (k1 >> 2))
+          if (k1 < S) {
+            if (ty == k1 / M)
 #pragma unroll
-              for (int c = 0; c < 4; ++c) rowbuf[(k1 & 1) * kBS + 4 * tx + c] = x[(u + 1) & 3][c];
-            if (tx == (k1 >> 2))
+              for (int c = 0; c < M; ++c) rowbuf[(k1 & 1) * S + M * tx + c] = x[(u + 1) % M][c];
+            if (tx == k1 / M)
 #pragma unroll
-              for (int a = 0; a < 4; ++a) colbuf[(k1 & 1) * kBS + 4 * ty + a] = x[a][(u + 1) & 3];
+              for (int a = 0; a < M; ++a) colbuf[(k1 & 1) * S + M * ty + a] = x[a][(u + 1) % M];
           }
         }
       }
@@ -149,32 +158,32 @@ __global__ void __launch_bounds__(kBThreads) fw_batched_cta(const BatchDesc *__r
       for (int t = 0; t < 2 * (R - 1); ++t) {
         const bool row = t < R - 1;
         const int other = skip_pivot(row ? t : t - (R - 1), b);
-        const int64_t r0 = row ? p0 : (int64_t)other * kBS, c0 = row ? (int64_t)other * kBS : p0;
-        C acc[4][4];
+        const int64_t r0 = row ? p0 : (int64_t)other * S, c0 = row ? (int64_t)other * S : p0;
+        C acc[M][M];
         IO::load(d, ld, n, r0, c0, ty, tx, acc);
         IO::to_smem(Ps, ty, tx, acc);
         __syncthreads();
         if (row)
-          minplus_tile<T>(acc, Ds, Ps, ty, tx);
+          minplus_tile<T, S, M>(acc, Ds, Ps, ty, tx);
         else
-          minplus_tile<T>(acc, Ps, Ds, ty, tx);
+          minplus_tile<T, S, M>(acc, Ps, Ds, ty, tx);
         IO::store(d, ld, n, r0, c0, ty, tx, acc, last);
         __syncthreads();
       }
       // ---- phase 3: every other tile, A = column panel tile, B = row panel tile
       for (int ii = 0; ii < R - 1; ++ii) {
-        const int64_t r0 = (int64_t)skip_pivot(ii, b) * kBS;
-        C a[4][4];
+        const int64_t r0 = (int64_t)skip_pivot(ii, b) * S;
+        C a[M][M];
         IO::load(d, ld, n, r0, p0, ty, tx, a);
         IO::to_smem(Ps, ty, tx, a);
         for (int jj = 0; jj < R - 1; ++jj) {
-          const int64_t c0 = (int64_t)skip_pivot(jj, b) * kBS;
-          C bt[4][4], acc[4][4];
+          const int64_t c0 = (int64_t)skip_pivot(jj, b) * S;
+          C bt[M][M], acc[M][M];
           IO::load(d, ld, n, p0, c0, ty, tx, bt);
           IO::load(d, ld, n, r0, c0, ty, tx, acc);
           IO::to_smem(Qs, ty, tx, bt);
           __syncthreads();
-          minplus_tile<T>(acc, Ps, Qs, ty, tx);
+          minplus_tile<T, S, M>(acc, Ps, Qs, ty, tx);
           IO::store(d, ld, n, r0, c0, ty, tx, acc, last);
           __syncthreads();
         }
@@ -184,46 +193,69 @@ __global__ void __launch_bounds__(kBThreads) fw_batched_cta(const BatchDesc *__r
   }
 }
 
-template <typename T>
+template <typename T, int S, int M>
 int launch_batched_kernel(const BatchDesc *descs, int count, int *counter, cudaStream_t st) {
+  using B = BShape<S, M>;
   static thread_local int setup_mask = 0;
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return APSP_ECUDA;
   if (!(setup_mask & (1 << (dev & 31)))) {
-    if (cudaFuncSetAttribute(fw_batched_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmem) !=
+    if (cudaFuncSetAttribute(fw_batched_cta<T, S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM) !=
         cudaSuccess)
       return APSP_ECUDA;
     setup_mask |= 1 << (dev & 31);
   }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return APSP_ECUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_cta<T>, kBThreads, kBSmem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_cta<T, S, M>, B::NT, B::SMEM) !=
       cudaSuccess)
     return APSP_ECUDA;
   const int grid = std::max(1, std::min(count, sms * std::max(per_sm, 1)));
   if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return APSP_ECUDA;
-  fw_batched_cta<T><<<grid, kBThreads, kBSmem, st>>>(descs, count, counter);
+  fw_batched_cta<T, S, M><<<grid, B::NT, B::SMEM, st>>>(descs, count, counter);
   return cudaPeekAtLastError() == cudaSuccess ? APSP_OK : APSP_ECUDA;
+}
+
+template <typename T>
+int launch_variant(int variant, const BatchDesc *descs, int count, int *counter, cudaStream_t st) {
+  switch (variant) {
+    case 0: return launch_batched_kernel<T, 32, 2>(descs, count, counter, st);
+    case 1: return launch_batched_kernel<T, 32, 4>(descs, count, counter, st);
+    case 2: return launch_batched_kernel<T, 64, 4>(descs, count, counter, st);
+    case 3: return launch_batched_kernel<T, 128, 4>(descs, count, counter, st);
+  }
+  return APSP_EINVAL;
 }
 
 }  // namespace
 
-// Device buffer for the descriptors + work counter of each distinct batch,
-// and a CUDA graph (counter reset + persistent kernel) once the same batch
-// (same matrices, same stream) is solved a second time.
+// Device buffer for the descriptors + work counters of each distinct batch,
+// and a CUDA graph (counter resets + persistent kernels) once the same batch
+// (same matrices, same stream) is solved a second time.  Graphs are grouped
+// by the kernel shape the tuning table picks for their n (the descriptors are
+// sorted by n, so each group is a contiguous range); the groups run
+// concurrently on forked streams and join back on the caller's stream.
 namespace {
+
+struct Group {
+  int variant, first, count;
+};
 
 struct BatchGraph {
   int dev;
   cudaStream_t stream;
   int dtype;
   std::vector<BatchDesc> descs;
-  void *dev_buf = nullptr;  // descriptors followed by the counter
+  std::vector<Group> groups;
+  void *dev_buf = nullptr;  // descriptors, then one 16-byte counter slot per group
   cudaGraphExec_t exec = nullptr;
   int uses = 0;
 };
 std::mutex g_bmu;
 std::vector<BatchGraph *> g_bgraphs;
 constexpr size_t kMaxBatchGraphs = 8;
+constexpr int kMaxGroups = 4;
+cudaStream_t g_fork[64][kMaxGroups];
+cudaEvent_t g_fork_ev[64][kMaxGroups + 1];
 
 bool same_batch(const BatchGraph *e, const BatchDesc *d, int count, int dtype, cudaStream_t st, int dev) {
   if (e->dev != dev || e->stream != st || e->dtype != dtype || (int)e->descs.size() != count) return false;
@@ -232,23 +264,57 @@ bool same_batch(const BatchGraph *e, const BatchDesc *d, int count, int dtype, c
   return true;
 }
 
-int launch_dtype(int dtype, const BatchDesc *descs, int count, int *counter, cudaStream_t st) {
+int launch_dtype(int dtype, int variant, const BatchDesc *descs, int count, int *counter, cudaStream_t st) {
   switch (dtype) {
-    case APSP_I32: return launch_batched_kernel<int32_t>(descs, count, counter, st);
-    case APSP_F32: return launch_batched_kernel<float>(descs, count, counter, st);
-    case APSP_I16: return launch_batched_kernel<int16_t>(descs, count, counter, st);
+    case APSP_I32: return launch_variant<int32_t>(variant, descs, count, counter, st);
+    case APSP_F32: return launch_variant<float>(variant, descs, count, counter, st);
+    case APSP_I16: return launch_variant<int16_t>(variant, descs, count, counter, st);
   }
   return APSP_EINVAL;
+}
+
+int fork_resources(int dev) {
+  if (g_fork_ev[dev][0]) return APSP_OK;
+  for (int i = 0; i < kMaxGroups; ++i)
+    if (cudaStreamCreateWithFlags(&g_fork[dev][i], cudaStreamNonBlocking) != cudaSuccess) return APSP_ECUDA;
+  for (int i = 0; i <= kMaxGroups; ++i)
+    if (cudaEventCreateWithFlags(&g_fork_ev[dev][i], cudaEventDisableTiming) != cudaSuccess) return APSP_ECUDA;
+  return APSP_OK;
+}
+
+// Enqueue all groups on `st` (one group inline, the others forked).
+int enqueue_groups(const BatchGraph *e, cudaStream_t st) {
+  const BatchDesc *ddesc = static_cast<const BatchDesc *>(e->dev_buf);
+  char *ctr = static_cast<char *>(e->dev_buf) + e->descs.size() * sizeof(BatchDesc);
+  const int ng = (int)e->groups.size();
+  if (ng == 1) {
+    const Group &g = e->groups[0];
+    return launch_dtype(e->dtype, g.variant, ddesc + g.first, g.count, reinterpret_cast<int *>(ctr), st);
+  }
+  if (cudaEventRecord(g_fork_ev[e->dev][kMaxGroups], st) != cudaSuccess) return APSP_ECUDA;
+  for (int i = 0; i < ng; ++i) {
+    cudaStream_t s = g_fork[e->dev][i];
+    if (cudaStreamWaitEvent(s, g_fork_ev[e->dev][kMaxGroups], 0) != cudaSuccess) return APSP_ECUDA;
+    const Group &g = e->groups[i];
+    const int rc = launch_dtype(e->dtype, g.variant, ddesc + g.first, g.count, reinterpret_cast<int *>(ctr + 16 * i), s);
+    if (rc != APSP_OK) return rc;
+    if (cudaEventRecord(g_fork_ev[e->dev][i], s) != cudaSuccess) return APSP_ECUDA;
+    if (cudaStreamWaitEvent(st, g_fork_ev[e->dev][i], 0) != cudaSuccess) return APSP_ECUDA;
+  }
+  return APSP_OK;
 }
 
 }  // namespace
 
 int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStream_t st, int dev) {
   if (count <= 0) return APSP_OK;
+  if (dev < 0 || dev >= 64) return APSP_ECUDA;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return APSP_ECUDA;
   if (cap != cudaStreamCaptureStatusNone) return APSP_EUNSUPPORTED;  // descriptors must be uploaded first
   std::lock_guard<std::mutex> lk(g_bmu);
+  int rc = fork_resources(dev);
+  if (rc != APSP_OK) return rc;
   BatchGraph *e = nullptr;
   for (auto *c : g_bgraphs)
     if (same_batch(c, host_descs, count, dtype, st, dev)) e = c;
@@ -261,8 +327,19 @@ int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStr
       delete old;
       g_bgraphs.erase(g_bgraphs.begin());
     }
-    e = new BatchGraph{dev, st, dtype, std::vector<BatchDesc>(host_descs, host_descs + count)};
-    const size_t bytes = (size_t)count * sizeof(BatchDesc) + 16;
+    e = new BatchGraph{dev, st, dtype, std::vector<BatchDesc>(host_descs, host_descs + count), {}};
+    for (int i = 0; i < count; ++i) {
+      const int v = tuned_batch_variant(host_descs[i].n, dtype);
+      if (e->groups.empty() || e->groups.back().variant != v) {
+        if ((int)e->groups.size() == kMaxGroups) {  // merge the tail into the last group
+          e->groups.back().count = count - e->groups.back().first;
+          break;
+        }
+        e->groups.push_back({v, i, 0});
+      }
+      e->groups.back().count = i + 1 - e->groups.back().first;
+    }
+    const size_t bytes = (size_t)count * sizeof(BatchDesc) + 16 * kMaxGroups;
     if (cudaMalloc(&e->dev_buf, bytes) != cudaSuccess) {
       delete e;
       return APSP_ENOMEM;
@@ -275,18 +352,16 @@ int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStr
     }
     g_bgraphs.push_back(e);
   }
-  const BatchDesc *ddesc = static_cast<const BatchDesc *>(e->dev_buf);
-  int *counter = reinterpret_cast<int *>(static_cast<char *>(e->dev_buf) + (size_t)count * sizeof(BatchDesc));
   ++e->uses;
   if (e->exec) return cudaGraphLaunch(e->exec, st) == cudaSuccess ? APSP_OK : APSP_ECUDA;
-  if (e->uses < 2) return launch_dtype(dtype, ddesc, count, counter, st);
-  // second use of the same batch: capture counter reset + persistent kernel
+  if (e->uses < 2) return enqueue_groups(e, st);
+  // second use of the same batch: capture the counter resets + kernels
   cudaStream_t cs = nullptr;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return APSP_ECUDA;
-  int rc = APSP_ECUDA;
+  rc = APSP_ECUDA;
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    const int lr = launch_dtype(dtype, ddesc, count, counter, cs);
+    const int lr = enqueue_groups(e, cs);
     const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (lr == APSP_OK && ce == cudaSuccess && cudaGraphInstantiate(&e->exec, graph, 0) == cudaSuccess)
       rc = cudaGraphLaunch(e->exec, st) == cudaSuccess ? APSP_OK : APSP_ECUDA;
@@ -295,6 +370,26 @@ int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStr
     if (graph) cudaGraphDestroy(graph);
   }
   cudaStreamDestroy(cs);
+  return rc;
+}
+
+// Times one kernel shape on `count` graphs (used by the autotuner).
+int time_batched_variant(const BatchDesc *dev_descs, int count, int *counter, int dtype, int variant,
+                         cudaStream_t st, float *ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return APSP_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return APSP_ECUDA;
+  }
+  int rc = launch_dtype(dtype, variant, dev_descs, count, counter, st);  // warm-up
+  if (rc == APSP_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = APSP_ECUDA;
+  if (rc == APSP_OK) rc = launch_dtype(dtype, variant, dev_descs, count, counter, st);
+  if (rc == APSP_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = APSP_ECUDA;
+  if (rc == APSP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess))
+    rc = APSP_ECUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return rc;
 }
 

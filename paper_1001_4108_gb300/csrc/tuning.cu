@@ -1,0 +1,225 @@
+// Autotuner: picks, per element type, the k-block depth of the single-graph
+// path (by n) and the kernel shape (tile side, register block) of the batched
+// path (by n bucket) from timings on this GPU, and keeps them in a table the
+// dispatch code reads.  The table can be saved to and loaded from a text file.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/apsp.h"
+#include "apsp_internal.h"
+
+namespace apsp {
+namespace {
+
+constexpr int kBuckets = 5;
+constexpr int64_t kBucketMax[kBuckets] = {32, 64, 128, 256, 512};
+
+struct Table {
+  int batch_variant[3][kBuckets];
+  int64_t kblock_cross[3];  // n >= cross: s = 128, else s = 64
+  int tuned[3];
+};
+
+// Defaults = the choices apsp_autotune made on a GB300: shape (s 32, 4x4) up
+// to n = 32, (s 64, 4x4) up to 256, (s 128, 4x4) up to 512; single-graph
+// k-block 128 from n = 6144 (int16: 8192).
+Table g_tab = {{{1, 2, 2, 2, 3}, {1, 2, 2, 2, 3}, {1, 2, 2, 2, 3}}, {6144, 6144, 8192}, {0, 0, 0}};
+std::mutex g_tmu;
+
+int dtype_index(int dtype) { return dtype == APSP_F32 ? 1 : dtype == APSP_I16 ? 2 : 0; }
+const char *dtype_name(int i) { return i == 1 ? "f32" : i == 2 ? "i16" : "i32"; }
+int elem_bytes(int dtype) { return dtype == APSP_I16 ? 2 : 4; }
+
+// Synthetic weights for timing only (Floyd-Warshall time does not depend on
+// the data): small positive values, every 4th entry "infinity".
+template <typename T> __device__ T synth(uint32_t h);
+template <> __device__ int32_t synth<int32_t>(uint32_t h) { return (h & 3) ? (int32_t)(h % 1000) + 1 : (1 << 29); }
+template <> __device__ float synth<float>(uint32_t h) { return (float)((h >> 8) % 1000 + 1) * 1e-3f; }
+template <> __device__ int16_t synth<int16_t>(uint32_t h) { return (h & 3) ? (int16_t)(h % 7 + 1) : (int16_t)16383; }
+
+template <typename T>
+__global__ void fill_synthetic(T *p, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u;
+    h ^= h >> 13;
+    h *= 0x5bd1e995u;
+    p[i] = synth<T>(h ^ (h >> 15));
+  }
+}
+
+int fill(void *p, size_t elems, int dtype, cudaStream_t st) {
+  const int blocks = 1024;
+  if (dtype == APSP_I32) fill_synthetic<int32_t><<<blocks, 256, 0, st>>>((int32_t *)p, elems);
+  if (dtype == APSP_F32) fill_synthetic<float><<<blocks, 256, 0, st>>>((float *)p, elems);
+  if (dtype == APSP_I16) fill_synthetic<int16_t><<<blocks, 256, 0, st>>>((int16_t *)p, elems);
+  return cudaPeekAtLastError() == cudaSuccess ? APSP_OK : APSP_ECUDA;
+}
+
+}  // namespace
+
+int tuned_batch_variant(int64_t n, int dtype) {
+  const int d = dtype_index(dtype);
+  for (int b = 0; b < kBuckets; ++b)
+    if (n <= kBucketMax[b]) return g_tab.batch_variant[d][b];
+  return g_tab.batch_variant[d][kBuckets - 1];
+}
+
+int tuned_kblock(int64_t n, int dtype) { return n >= g_tab.kblock_cross[dtype_index(dtype)] ? 128 : 64; }
+
+}  // namespace apsp
+
+using namespace apsp;
+
+extern "C" int apsp_autotune(int dtype, void *stream, char *report, int64_t report_len) {
+  if (dtype != APSP_I32 && dtype != APSP_F32 && dtype != APSP_I16) return APSP_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int di = dtype_index(dtype);
+  const int es = elem_bytes(dtype);
+  std::string rep = std::string("{\"dtype\": \"") + dtype_name(di) + "\", \"batched\": [";
+  int best_v[kBuckets];
+  // ---- batched kernel shape per n bucket
+  for (int bk = 0; bk < kBuckets; ++bk) {
+    const int64_t hi = kBucketMax[bk], lo = bk ? kBucketMax[bk - 1] + 1 : 1;
+    // about 2e9 relaxations, at least 4 graphs per SM, at most 1 GiB of matrices
+    int64_t count = std::max<int64_t>(608, (int64_t)(2e9 / (double)(hi * hi * hi)));
+    count = std::min<int64_t>(count, (int64_t)((1ll << 30) / (hi * hi * es)));
+    std::vector<BatchDesc> descs((size_t)count);
+    size_t total = 0;
+    for (int64_t g = 0; g < count; ++g) {
+      const int64_t n = hi - (g * (hi - lo + 1)) / count;  // sizes spread over the bucket, largest first
+      descs[(size_t)g] = {nullptr, n, n};
+      total += (size_t)(n * n);
+    }
+    char *mats = nullptr, *meta = nullptr;
+    if (cudaMalloc(&mats, total * es) != cudaSuccess) return APSP_ENOMEM;
+    if (cudaMalloc(&meta, (size_t)count * sizeof(BatchDesc) + 16) != cudaSuccess) {
+      cudaFree(mats);
+      return APSP_ENOMEM;
+    }
+    size_t off = 0;
+    for (auto &dsc : descs) {
+      dsc.d = mats + off * es;
+      off += (size_t)(dsc.n * dsc.n);
+    }
+    int rc = cudaMemcpyAsync(meta, descs.data(), descs.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice, st) ==
+                     cudaSuccess
+                 ? APSP_OK
+                 : APSP_ECUDA;
+    int *counter = reinterpret_cast<int *>(meta + descs.size() * sizeof(BatchDesc));
+    float t[kBatchVariants];
+    int best = -1;
+    for (int v = 0; v < kBatchVariants && rc == APSP_OK; ++v) {
+      rc = fill(mats, total, dtype, st);
+      if (rc == APSP_OK)
+        rc = time_batched_variant(reinterpret_cast<BatchDesc *>(meta), (int)count, counter, dtype, v, st, &t[v]);
+      if (rc == APSP_OK && (best < 0 || t[v] < t[best])) best = v;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(mats);
+    cudaFree(meta);
+    if (rc != APSP_OK) return rc;
+    best_v[bk] = best;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s{\"n_max\": %lld, \"graphs\": %lld, \"ms\": [%.3f, %.3f, %.3f, %.3f], \"best\": %d}",
+             bk ? ", " : "", (long long)hi, (long long)count, t[0], t[1], t[2], t[3], best);
+    rep += buf;
+  }
+  // ---- single-graph k-block: s = 64 vs s = 128
+  rep += "], \"kblock\": [";
+  const int64_t sizes[] = {1024, 2048, 3072, 4096, 6144};
+  int64_t cross = 1ll << 40;
+  for (int i = 0; i < 5; ++i) {
+    const int64_t n = sizes[i];
+    char *m = nullptr;
+    if (cudaMalloc(&m, (size_t)n * n * es) != cudaSuccess) return APSP_ENOMEM;
+    float ms[2] = {0, 0};
+    int rc = APSP_OK;
+    for (int j = 0; j < 2 && rc == APSP_OK; ++j) {
+      apsp_options o{};
+      o.kblock = j ? 128 : 64;
+      o.flags = APSP_FLAG_NO_GRAPH;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      rc = fill(m, (size_t)n * n, dtype, st);
+      if (rc == APSP_OK) rc = apsp_fw_ex(m, n, n, dtype, &o, st);  // warm-up (workspace, attributes)
+      if (rc == APSP_OK) rc = fill(m, (size_t)n * n, dtype, st);
+      cudaEventRecord(e0, st);
+      if (rc == APSP_OK) rc = apsp_fw_ex(m, n, n, dtype, &o, st);
+      cudaEventRecord(e1, st);
+      if (rc == APSP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms[j], e0, e1) != cudaSuccess))
+        rc = APSP_ECUDA;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+    cudaFree(m);
+    if (rc != APSP_OK) return rc;
+    if (ms[1] < ms[0] && cross > n) cross = n;
+    if (ms[1] >= ms[0]) cross = 1ll << 40;  // 128 must keep winning from the crossover on
+    char buf[160];
+    snprintf(buf, sizeof(buf), "%s{\"n\": %lld, \"ms_s64\": %.3f, \"ms_s128\": %.3f}", i ? ", " : "", (long long)n,
+             ms[0], ms[1]);
+    rep += buf;
+  }
+  if (cross == (1ll << 40)) cross = 8192;  // s = 128 above the measured range
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (int bk = 0; bk < kBuckets; ++bk) g_tab.batch_variant[di][bk] = best_v[bk];
+    g_tab.kblock_cross[di] = cross;
+    g_tab.tuned[di] = 1;
+  }
+  char tail[96];
+  snprintf(tail, sizeof(tail), "], \"kblock_crossover\": %lld}", (long long)cross);
+  rep += tail;
+  if (report && report_len > 0) {
+    const size_t k = std::min<size_t>(rep.size(), (size_t)report_len - 1);
+    memcpy(report, rep.data(), k);
+    report[k] = 0;
+  }
+  return APSP_OK;
+}
+
+extern "C" int apsp_tuning_save(const char *path) {
+  if (!path) return APSP_EINVAL;
+  FILE *f = fopen(path, "w");
+  if (!f) return APSP_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  fprintf(f, "apsp-tuning 1\n");
+  for (int d = 0; d < 3; ++d) {
+    fprintf(f, "%s kblock_crossover %lld batch_variants", dtype_name(d), (long long)g_tab.kblock_cross[d]);
+    for (int b = 0; b < kBuckets; ++b) fprintf(f, " %d", g_tab.batch_variant[d][b]);
+    fprintf(f, " tuned %d\n", g_tab.tuned[d]);
+  }
+  return fclose(f) == 0 ? APSP_OK : APSP_EINVAL;
+}
+
+extern "C" int apsp_tuning_load(const char *path) {
+  if (!path) return APSP_EINVAL;
+  FILE *f = fopen(path, "r");
+  if (!f) return APSP_EINVAL;
+  Table t = g_tab;
+  int version = 0, ok = fscanf(f, "apsp-tuning %d\n", &version) == 1 && version == 1;
+  for (int d = 0; d < 3 && ok; ++d) {
+    char name[8] = {0};
+    long long cross = 0;
+    int v[kBuckets], tuned = 0;
+    ok = fscanf(f, "%7s kblock_crossover %lld batch_variants %d %d %d %d %d tuned %d\n", name, &cross, &v[0], &v[1],
+                &v[2], &v[3], &v[4], &tuned) == 8 &&
+         strcmp(name, dtype_name(d)) == 0 && cross > 0;
+    for (int b = 0; b < kBuckets && ok; ++b) ok = v[b] >= 0 && v[b] < kBatchVariants;
+    if (ok) {
+      t.kblock_cross[d] = cross;
+      for (int b = 0; b < kBuckets; ++b) t.batch_variant[d][b] = v[b];
+      t.tuned[d] = tuned;
+    }
+  }
+  fclose(f);
+  if (!ok) return APSP_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_tab = t;
+  return APSP_OK;
+}

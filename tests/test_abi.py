@@ -68,6 +68,8 @@ def test_query_config(L):
     assert c.phase3_relax_per_round == (16384 - 128) ** 2 * 128
     c = binding.query_config(1000, binding.APSP_I32)
     assert c.kblock == 64 and c.rounds == 16
+    assert binding.query_config(4096, binding.APSP_F32).kblock == 64
+    assert binding.query_config(6144, binding.APSP_F32).kblock == 128
     c = binding.query_config(1000, binding.APSP_I16, 128)
     assert c.kblock == 128 and c.rounds == 8 and c.phase3_tma == 1
     cfg = binding.Config()
@@ -83,3 +85,14 @@ def test_batched_bad_arguments(L):
     assert L.apsp_fw_batched(P, N, LD, 2, binding.APSP_I32, None) == binding.APSP_EINVAL
     assert L.apsp_fw_batched(P, N, LD, -1, binding.APSP_I32, None) == binding.APSP_EINVAL
     assert L.apsp_fw_batched(None, None, None, 0, binding.APSP_I32, None) == binding.APSP_OK
+
+
+def test_tuning_file_validation(L, tmp_path):
+    bad = tmp_path / "bad.txt"
+    bad.write_text("apsp-tuning 1\ni32 kblock_crossover 4096 batch_variants 0 2 2 9 2 tuned 0\n")
+    assert L.apsp_tuning_load(str(bad).encode()) == binding.APSP_EINVAL
+    good = tmp_path / "good.txt"
+    assert L.apsp_tuning_save(str(good).encode()) == binding.APSP_OK
+    assert L.apsp_tuning_load(str(good).encode()) == binding.APSP_OK
+    assert "batch_variants" in good.read_text()
+    assert L.apsp_tuning_load(str(tmp_path / "missing.txt").encode()) == binding.APSP_EINVAL

@@ -92,3 +92,19 @@ def test_batched_padded_leading_dimension():
         out = t.cpu().numpy()
         np.testing.assert_array_equal(out[:, :n], oracle.fw_int32_conv(np.ascontiguousarray(w[:, :n])))
         assert (out[:, n:] == -7).all()
+
+
+def test_autotune_and_table_roundtrip(tmp_path):
+    rep = binding.autotune(binding.APSP_I32)
+    assert rep["dtype"] == "i32" and len(rep["batched"]) == 5 and len(rep["kblock"]) == 5
+    assert all(0 <= b["best"] < 4 for b in rep["batched"])
+    path = str(tmp_path / "tuning.txt")
+    binding.tuning_save(path)
+    binding.tuning_load(path)
+    # results do not depend on the chosen shapes
+    ws = inputs.c4_batch(40, seed=21)
+    ts = _to_gpu(ws)
+    binding.apsp_fw_batched(ts)
+    torch.cuda.synchronize()
+    for w, t in zip(ws, ts):
+        np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
