@@ -218,6 +218,63 @@ APSP_API int apsp_autotune(int dtype, void *stream, char *report, int64_t report
 APSP_API int apsp_tuning_save(const char *path);
 APSP_API int apsp_tuning_load(const char *path);
 
+/*
+ * Serving: a request loop with continuous batching.  apsp_submit copies the
+ * request's host matrix and queues it; a scheduler thread of the server admits
+ * queued requests oldest first while an in-flight slot is free and the
+ * request's device footprint fits the HBM budget, uploads each admitted matrix
+ * once and solves it on the device (requests with n <= 512 admitted together
+ * share one batched launch; larger ones run on their own streams, so requests
+ * overlap on the GPU), copies the result back and releases the device memory.
+ * apsp_poll / apsp_wait deliver a finished result into the caller's buffer and
+ * retire the ticket.  The kernels depend only on (n, dtype): a result is the
+ * same whether the request was solved alone or among others.  Latency is
+ * measured from submit to the result being in host memory.
+ */
+typedef struct apsp_server apsp_server;  /* opaque, owned by the library */
+
+typedef struct apsp_server_config {
+    int32_t device;            /* CUDA device ordinal                                    */
+    int32_t max_inflight;      /* requests on the GPU at once (slots), > 0               */
+    int64_t hbm_budget_bytes;  /* device bytes the resident matrices may take, > 0       */
+    int32_t streams;           /* streams for large requests (0 = 4)                     */
+    int32_t flags;             /* reserved, 0                                            */
+    int64_t max_n;             /* largest n accepted; sizes the per-stream workspaces     */
+} apsp_server_config;
+
+typedef struct apsp_stats {
+    int64_t submitted, completed, failed, queued, inflight;
+    int64_t bytes_resident;
+    double p50_ms, p99_ms, mean_ms;  /* latency, submit -> result in host memory */
+    double graphs_per_s;             /* completed / (last completion - first submit) */
+} apsp_stats;
+
+/* Creates a server (its scheduler thread, streams and workspaces). */
+APSP_API int apsp_server_create(apsp_server **out, const apsp_server_config *cfg);
+
+/* Queues one request; the matrix (host memory, row-major, leading dimension
+   ld >= n) is copied before the call returns.  *ticket identifies it.
+   APSP_ENOMEM if the matrix alone exceeds the HBM budget, APSP_EUNSUPPORTED
+   if n > max_n, APSP_EBUSY if the server is shutting down. */
+APSP_API int apsp_submit(apsp_server *srv, const void *host_dist, int64_t n, int64_t ld, int dtype, int flags,
+                         uint64_t *ticket);
+
+/* APSP_EPENDING while the request runs; otherwise delivers the distances
+   into out_dist (host, leading dimension out_ld >= n; NULL = discard) and
+   retires the ticket, returning APSP_OK or the request's error. */
+APSP_API int apsp_poll(apsp_server *srv, uint64_t ticket, void *out_dist, int64_t out_ld);
+
+/* apsp_poll that blocks up to timeout_us microseconds (< 0: no limit);
+   APSP_ETIMEOUT if the request is still running then. */
+APSP_API int apsp_wait(apsp_server *srv, uint64_t ticket, void *out_dist, int64_t out_ld, int64_t timeout_us);
+
+/* Counters and latency percentiles; reset != 0 clears them afterwards. */
+APSP_API int apsp_server_stats(apsp_server *srv, apsp_stats *out, int reset);
+
+/* Stops admitting, waits for in-flight requests, fails queued ones, frees
+   everything (undelivered results are dropped). */
+APSP_API int apsp_server_destroy(apsp_server *srv);
+
 /* Fills *cfg with the configuration apsp_fw would use (no device work). */
 APSP_API int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_config *cfg);
 

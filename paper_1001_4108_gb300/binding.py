@@ -26,7 +26,8 @@ INF_I16 = 16383
 EXPORTS = ["apsp_status_str", "apsp_version", "apsp_fw", "apsp_fw_ex", "apsp_fw_host",
            "apsp_workspace_bytes", "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus",
            "apsp_fw_f32_noalloc", "apsp_fw_batched", "apsp_autotune", "apsp_tuning_save",
-           "apsp_tuning_load"]
+           "apsp_tuning_load", "apsp_server_create", "apsp_submit", "apsp_poll", "apsp_wait",
+           "apsp_server_stats", "apsp_server_destroy"]
 
 
 class Options(ctypes.Structure):
@@ -39,6 +40,19 @@ class Config(ctypes.Structure):
     _fields_ = [("kblock", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("phase3_tma", ctypes.c_int32), ("phase3_threads", ctypes.c_int32),
                 ("phase3_relax_per_round", ctypes.c_int64)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("max_n", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("inflight", ctypes.c_int64), ("bytes_resident", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("graphs_per_s", ctypes.c_double)]
 
 
 class ApspError(RuntimeError):
@@ -77,6 +91,12 @@ def lib() -> ctypes.CDLL:
             L.apsp_fw_host.argtypes = [vp, i64, i64, i32, vp]
             L.apsp_fw_f32_noalloc.argtypes = [vp, i64, i64, vp]
             L.apsp_autotune.argtypes = [i32, vp, ctypes.c_char_p, i64]
+            L.apsp_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)]
+            L.apsp_submit.argtypes = [vp, vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+            L.apsp_poll.argtypes = [vp, ctypes.c_uint64, vp, i64]
+            L.apsp_wait.argtypes = [vp, ctypes.c_uint64, vp, i64, i64]
+            L.apsp_server_stats.argtypes = [vp, ctypes.POINTER(Stats), i32]
+            L.apsp_server_destroy.argtypes = [vp]
             L.apsp_tuning_save.argtypes = [ctypes.c_char_p]
             L.apsp_tuning_load.argtypes = [ctypes.c_char_p]
             L.apsp_fw_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
@@ -231,3 +251,70 @@ def ubench(form: int, iters: int, sink, blocks: int = 0, threads: int = 256, str
     _check(lib().apsp_ubench_minplus(form, iters, blocks, threads, sink.data_ptr(),
                                      _stream_handle(stream), ctypes.byref(out)), "apsp_ubench_minplus")
     return out.value
+
+
+class Server:
+    """Serving handle (apsp_server_*): submit host matrices, poll / wait for
+    the distances.  Use as a context manager or call close()."""
+
+    def __init__(self, device: int = 0, max_inflight: int = 64, hbm_budget_bytes: int = 8 << 30,
+                 streams: int = 4, max_n: int = 16384):
+        self._h = ctypes.c_void_p()
+        cfg = ServerConfig(device, max_inflight, hbm_budget_bytes, streams, 0, max_n)
+        _check(lib().apsp_server_create(ctypes.byref(self._h), ctypes.byref(cfg)), "apsp_server_create")
+        self._shapes = {}
+
+    def submit(self, a) -> int:
+        """Queue a numpy matrix (copied before return); returns the ticket."""
+        import numpy as np
+        assert isinstance(a, np.ndarray) and a.ndim == 2
+        t = ctypes.c_uint64()
+        n = a.shape[0]
+        if n:
+            assert a.strides[1] == a.itemsize, "row-major matrix with unit column stride expected"
+        ld = a.strides[0] // a.itemsize if n else 0
+        _check(lib().apsp_submit(self._h, a.ctypes.data, n, ld, dtype_code(a.dtype), 0, ctypes.byref(t)),
+               "apsp_submit")
+        self._shapes[t.value] = (n, a.dtype)
+        return t.value
+
+    def _out(self, ticket):
+        import numpy as np
+        n, dt = self._shapes[ticket]
+        return np.empty((n, n), dtype=dt)
+
+    def poll(self, ticket: int):
+        """The result (numpy) if finished, else None."""
+        out = self._out(ticket)
+        st = lib().apsp_poll(self._h, ticket, out.ctypes.data, out.shape[0])
+        if st == APSP_EPENDING:
+            return None
+        self._shapes.pop(ticket, None)
+        _check(st, "apsp_poll")
+        return out
+
+    def wait(self, ticket: int, timeout_s: float | None = None):
+        out = self._out(ticket)
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        st = lib().apsp_wait(self._h, ticket, out.ctypes.data, out.shape[0], us)
+        if st == APSP_ETIMEOUT:
+            return None
+        self._shapes.pop(ticket, None)
+        _check(st, "apsp_wait")
+        return out
+
+    def stats(self, reset: bool = False) -> dict:
+        s = Stats()
+        _check(lib().apsp_server_stats(self._h, ctypes.byref(s), 1 if reset else 0), "apsp_server_stats")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().apsp_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

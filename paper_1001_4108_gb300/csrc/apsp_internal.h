@@ -54,6 +54,8 @@ int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStr
 constexpr int kBatchVariants = 4;
 int tuned_batch_variant(int64_t n, int dtype);
 int tuned_kblock(int64_t n, int dtype);
+int run_batched_direct(const BatchDesc *host_descs, int count, int dtype, cudaStream_t st, void **dev_buf,
+                       size_t *cap);
 int time_batched_variant(const BatchDesc *dev_descs, int count, int *counter, int dtype, int variant,
                          cudaStream_t st, float *ms);
 

@@ -373,6 +373,42 @@ int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStr
   return rc;
 }
 
+// Batched launch without caching (the serving loop's path): uploads the
+// descriptors (sorted by n, largest first) into a device buffer grown in
+// stream order, then launches one persistent kernel per kernel-shape group, in
+// order, on `st`.
+int run_batched_direct(const BatchDesc *host_descs, int count, int dtype, cudaStream_t st, void **dev_buf,
+                       size_t *cap) {
+  if (count <= 0) return APSP_OK;
+  const size_t need = (size_t)count * sizeof(BatchDesc) + 16 * kBatchVariants * 2;
+  if (*cap < need) {
+    if (*dev_buf) cudaFreeAsync(*dev_buf, st);
+    *dev_buf = nullptr;
+    *cap = 0;
+    size_t c = 4096;
+    while (c < need) c <<= 1;
+    if (cudaMallocAsync(dev_buf, c, st) != cudaSuccess) return APSP_ENOMEM;
+    *cap = c;
+  }
+  // pageable source: the runtime stages it before returning
+  if (cudaMemcpyAsync(*dev_buf, host_descs, (size_t)count * sizeof(BatchDesc), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return APSP_ECUDA;
+  const BatchDesc *dd = static_cast<const BatchDesc *>(*dev_buf);
+  char *ctr = static_cast<char *>(*dev_buf) + (size_t)count * sizeof(BatchDesc);
+  int first = 0, slot = 0;
+  while (first < count) {
+    const int v = tuned_batch_variant(host_descs[first].n, dtype);
+    int last = first + 1;
+    while (last < count && tuned_batch_variant(host_descs[last].n, dtype) == v) ++last;
+    const int rc = launch_dtype(dtype, v, dd + first, last - first, reinterpret_cast<int *>(ctr + 16 * slot), st);
+    if (rc != APSP_OK) return rc;
+    slot = (slot + 1) % (2 * kBatchVariants);
+    first = last;
+  }
+  return APSP_OK;
+}
+
 // Times one kernel shape on `count` graphs (used by the autotuner).
 int time_batched_variant(const BatchDesc *dev_descs, int count, int *counter, int dtype, int variant,
                          cudaStream_t st, float *ms) {

@@ -96,3 +96,13 @@ def test_tuning_file_validation(L, tmp_path):
     assert L.apsp_tuning_load(str(good).encode()) == binding.APSP_OK
     assert "batch_variants" in good.read_text()
     assert L.apsp_tuning_load(str(tmp_path / "missing.txt").encode()) == binding.APSP_EINVAL
+
+
+def test_server_bad_config(L):
+    h = ctypes.c_void_p()
+    cfg = binding.ServerConfig(0, 0, 1 << 20, 0, 0, 1024)  # no slots
+    assert L.apsp_server_create(ctypes.byref(h), ctypes.byref(cfg)) == binding.APSP_EINVAL
+    cfg = binding.ServerConfig(0, 4, 0, 0, 0, 1024)  # no memory
+    assert L.apsp_server_create(ctypes.byref(h), ctypes.byref(cfg)) == binding.APSP_EINVAL
+    assert L.apsp_poll(None, 1, None, 0) == binding.APSP_EINVAL
+    assert L.apsp_server_destroy(None) == binding.APSP_EINVAL
