@@ -46,6 +46,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--batched", type=int, default=4096, help="graphs in the batched (c4) comparison; 0 = skip")
+    ap.add_argument("--serving", type=int, default=240, help="requests in the serving (c5) sweep; 0 = skip")
     return ap.parse_args()
 
 
@@ -234,6 +235,110 @@ def bench_batched(count: int = 4096, steps: int = 3, seed: int = 5):
             "autotuned_shapes": {str(b["n_max"]): b["best"] for b in tuning["batched"]}}
 
 
+def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), server_factory=None,
+                  solve_host=None, time_limit_s: float = 600.0):
+    """Serving form (c5): Poisson arrivals, n log-uniform in [32, 4096], half
+    int32 graphs (edge probability 0.05-0.5), half complete fp32 graphs.  The
+    server (continuous batching, admission by HBM footprint) against plain
+    per-request launches (one apsp_fw_host call at a time, in arrival order),
+    at rates that are fractions of the server's measured saturation rate.
+    `server_factory` / `solve_host` replace the library (control-flow tests)."""
+    import threading
+    import numpy as np
+    from paper_1001_4108_gb300 import inputs
+    if server_factory is None or solve_host is None:
+        from paper_1001_4108_gb300 import binding
+        server_factory = server_factory or (lambda: binding.Server(max_inflight=64, hbm_budget_bytes=16 << 30,
+                                                                   max_n=4096))
+        solve_host = solve_host or binding.apsp_fw_host
+    reqs = inputs.c5_requests(count, rate_hz=1.0, seed=seed)
+    mats = [r.w for r in reqs]
+    t_start = time.perf_counter()
+
+    def check_time():
+        if time.perf_counter() - t_start > time_limit_s:
+            raise TimeoutError("serving benchmark exceeded its time limit")
+
+    def pct(v, p):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(p * (len(v) - 1) + 0.5))] if v else None
+
+    def run_server(arrivals):
+        m = len(arrivals)
+        with server_factory() as srv:
+            tickets = [None] * m
+            errors = []
+            t0 = time.perf_counter()
+
+            def submitter():
+                try:
+                    for i in range(m):
+                        dt = arrivals[i] - (time.perf_counter() - t0)
+                        if dt > 0:
+                            time.sleep(dt)
+                        tickets[i] = srv.submit(mats[i])
+                except BaseException as e:  # surfaced by the collector below
+                    errors.append(e)
+            th = threading.Thread(target=submitter, daemon=True)
+            th.start()
+            outs = [None] * m
+            for i in range(m):
+                while tickets[i] is None:
+                    if errors:
+                        raise errors[0]
+                    if not th.is_alive() and tickets[i] is None:
+                        raise RuntimeError("submitter stopped early")
+                    check_time()
+                    time.sleep(0.0002)
+                outs[i] = srv.wait(tickets[i], timeout_s=max(1.0, time_limit_s - (time.perf_counter() - t_start)))
+                if outs[i] is None:
+                    raise TimeoutError("request did not finish")
+            th.join()
+            st = srv.stats()
+        return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "graphs_per_s": st["graphs_per_s"]}, outs
+
+    def run_plain(arrivals):
+        lat, outs = [], []
+        t0 = time.perf_counter()
+        for i in range(len(arrivals)):
+            check_time()
+            dt = arrivals[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            a = mats[i].copy()
+            solve_host(a)
+            lat.append((time.perf_counter() - t0 - arrivals[i]) * 1e3)
+            outs.append(a)
+        span = time.perf_counter() - t0
+        return {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "graphs_per_s": len(arrivals) / span}, outs
+
+    # warm-up (kernels, workspaces, pinned buffers), then saturation: all requests at t = 0
+    run_server([0.0] * min(count, 24))
+    sat, outs_s = run_server([0.0] * count)
+    base, outs_p = run_plain([0.0] * count)
+    exact = True
+    for r, x, y in zip(reqs, outs_s, outs_p):
+        if r.dtype == "i32":
+            exact &= bool(np.array_equal(x, y))
+        else:
+            fin = np.isfinite(y)
+            exact &= bool((np.abs(x[fin].astype(np.float64) - y[fin]) <= 1e-5 * np.abs(y[fin])).all())
+    g = inputs.rng(seed + 1)
+    sweep = []
+    for f in rates:
+        rate = f * sat["graphs_per_s"]
+        gaps = g.exponential(1.0 / rate, size=count)
+        arr = list(np.cumsum(gaps) - gaps[0])
+        srv_res, _ = run_server(arr)
+        plain_res, _ = run_plain(arr)
+        sweep.append({"rate_per_s": rate, "fraction_of_saturation": f, "server": srv_res, "plain": plain_res})
+    return {"workload": f"c5: {count} requests, n log-uniform in [32,4096], half int32 (edge probability "
+                        "0.05-0.5, weights [1,1000]), half complete fp32 (weights (0,1])",
+            "saturation": {"server": sat, "plain": base},
+            "sweep": sweep, "same_results_as_plain": exact,
+            "latency": "submit (arrival) -> result in host memory"}
+
+
 def run_reference(a):
     rank, world, _ = _dist_env()
     if rank != 0:
@@ -408,6 +513,8 @@ def run_ours(a):
     }
     if a.batched > 0:
         line["batched"] = bench_batched(a.batched)
+    if a.serving > 0:
+        line["serving"] = bench_serving(a.serving)
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a.dtype)
     print(json.dumps(line), flush=True)
