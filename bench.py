@@ -312,8 +312,11 @@ def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), 
         span = time.perf_counter() - t0
         return {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "graphs_per_s": len(arrivals) / span}, outs
 
-    # warm-up (kernels, workspaces, pinned buffers), then saturation: all requests at t = 0
-    run_server([0.0] * min(count, 24))
+    # warm-up of both paths over the whole request set (kernels, workspaces,
+    # pinned buffers, the host path's device buffer), then saturation: all
+    # requests at t = 0
+    run_server([0.0] * count)
+    run_plain([0.0] * min(count, 48))
     sat, outs_s = run_server([0.0] * count)
     base, outs_p = run_plain([0.0] * count)
     exact = True
