@@ -136,6 +136,21 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+def max_over_ranks(x: float, device: str) -> float:
+    """The largest value of x over all ranks of the default process group (the
+    whole job is as slow as its slowest replica)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed / the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -435,13 +450,11 @@ def run_ours(a):
     clocks = sampler.stop() if sampler else None
     if world > 1:
         dist.barrier()
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
     assert binding.device_error() == 0
 
     relax_per_step = float(n) ** 3
-    value = world * a.steps * relax_per_step / (total_ms * 1e-3)
+    value = job_value(a.steps * relax_per_step, world, total_ms * 1e-3)
 
     # e2e: the host entry point (pinned host matrix -> H2D -> solve -> D2H)
     e2e = None

@@ -24,10 +24,11 @@ struct Table {
   int tuned[3];
 };
 
-// Defaults = the choices apsp_autotune made on a GB300: shape (s 32, 4x4) up
-// to n = 32, (s 64, 4x4) up to 256, (s 128, 4x4) up to 512; single-graph
-// k-block 128 from n = 6144 (int16: 8192).
-Table g_tab = {{{1, 2, 2, 2, 3}, {1, 2, 2, 2, 3}, {1, 2, 2, 2, 3}}, {6144, 6144, 8192}, {0, 0, 0}};
+// Defaults = choices measured on a GB300: shape (s 32, 4x4) up to n = 32,
+// (s 64, 4x4) up to 512 (on a mixed batch it beats using (s 128, 4x4) above
+// 256, which wins only when those graphs run alone); single-graph k-block 128
+// from n = 6144 (int16: 8192).
+Table g_tab = {{{1, 2, 2, 2, 2}, {1, 2, 2, 2, 2}, {1, 2, 2, 2, 2}}, {6144, 6144, 8192}, {0, 0, 0}};
 std::mutex g_tmu;
 
 int dtype_index(int dtype) { return dtype == APSP_F32 ? 1 : dtype == APSP_I16 ? 2 : 0; }
@@ -127,6 +128,76 @@ extern "C" int apsp_autotune(int dtype, void *stream, char *report, int64_t repo
     snprintf(buf, sizeof(buf), "%s{\"n_max\": %lld, \"graphs\": %lld, \"ms\": [%.3f, %.3f, %.3f, %.3f], \"best\": %d}",
              bk ? ", " : "", (long long)hi, (long long)count, t[0], t[1], t[2], t[3], best);
     rep += buf;
+  }
+  // ---- whole-batch assignment: the groups of a batch run concurrently and
+  // compete for the SMs, so the per-bucket winners are checked against a few
+  // fixed assignments on a mixed batch (n uniform in 16..512, largest first)
+  rep += "], \"mixed\": [";
+  {
+    const int cand[][kBuckets] = {{best_v[0], best_v[1], best_v[2], best_v[3], best_v[4]},
+                                  {1, 2, 2, 2, 2}, {1, 2, 2, 2, 3}, {0, 2, 2, 2, 2}, {2, 2, 2, 2, 2}, {1, 1, 2, 2, 2}};
+    const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
+    const int count = 1024;
+    std::vector<BatchDesc> descs(count);
+    size_t total = 0;
+    for (int g = 0; g < count; ++g) {
+      const int64_t n = 512 - ((int64_t)g * (512 - 16 + 1)) / count;
+      descs[(size_t)g] = {nullptr, n, n};
+      total += (size_t)(n * n);
+    }
+    char *mats = nullptr;
+    if (cudaMalloc(&mats, total * es) != cudaSuccess) return APSP_ENOMEM;
+    size_t off = 0;
+    for (auto &dsc : descs) {
+      dsc.d = mats + off * es;
+      off += (size_t)(dsc.n * dsc.n);
+    }
+    void *dbuf = nullptr;
+    size_t dcap = 0;
+    Table saved;
+    {
+      std::lock_guard<std::mutex> lk(g_tmu);
+      saved = g_tab;
+    }
+    int best = -1, rc = APSP_OK;
+    float tbest = 0;
+    for (int c = 0; c < ncand && rc == APSP_OK; ++c) {
+      {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        for (int bk = 0; bk < kBuckets; ++bk) g_tab.batch_variant[di][bk] = cand[c][bk];
+      }
+      float ms = 0;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      rc = fill(mats, total, dtype, st);
+      if (rc == APSP_OK) rc = run_batched_direct(descs.data(), count, dtype, st, &dbuf, &dcap);  // warm-up
+      if (rc == APSP_OK) rc = fill(mats, total, dtype, st);
+      cudaEventRecord(e0, st);
+      if (rc == APSP_OK) rc = run_batched_direct(descs.data(), count, dtype, st, &dbuf, &dcap);
+      cudaEventRecord(e1, st);
+      if (rc == APSP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = APSP_ECUDA;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (rc == APSP_OK && (best < 0 || ms < tbest)) {
+        best = c;
+        tbest = ms;
+      }
+      char buf[160];
+      snprintf(buf, sizeof(buf), "%s{\"shapes\": [%d, %d, %d, %d, %d], \"ms\": %.3f}", c ? ", " : "", cand[c][0],
+               cand[c][1], cand[c][2], cand[c][3], cand[c][4], ms);
+      rep += buf;
+    }
+    cudaStreamSynchronize(st);
+    if (dbuf) cudaFree(dbuf);
+    cudaFree(mats);
+    {
+      std::lock_guard<std::mutex> lk(g_tmu);
+      g_tab = saved;
+    }
+    if (rc != APSP_OK) return rc;
+    for (int bk = 0; bk < kBuckets; ++bk) best_v[bk] = cand[best][bk];
   }
   // ---- single-graph k-block: s = 64 vs s = 128
   rep += "], \"kblock\": [";
