@@ -279,9 +279,17 @@ def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), 
         return v[min(len(v) - 1, int(p * (len(v) - 1) + 0.5))] if v else None
 
     def run_server(arrivals):
+        # Latency is taken on the client, from the scheduled arrival to the
+        # result in the caller's array, as for the plain path: it includes any
+        # delay of the submitting thread (apsp_submit copies the matrix) and
+        # the copy out.  Results are collected by a pool of waiters, so a
+        # finished small request is not held behind an earlier large one.
+        from concurrent.futures import ThreadPoolExecutor
         m = len(arrivals)
         with server_factory() as srv:
             tickets = [None] * m
+            done = [None] * m
+            outs = [None] * m
             errors = []
             t0 = time.perf_counter()
 
@@ -292,12 +300,10 @@ def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), 
                         if dt > 0:
                             time.sleep(dt)
                         tickets[i] = srv.submit(mats[i])
-                except BaseException as e:  # surfaced by the collector below
+                except BaseException as e:  # surfaced by the waiters below
                     errors.append(e)
-            th = threading.Thread(target=submitter, daemon=True)
-            th.start()
-            outs = [None] * m
-            for i in range(m):
+
+            def waiter(i):
                 while tickets[i] is None:
                     if errors:
                         raise errors[0]
@@ -305,12 +311,23 @@ def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), 
                         raise RuntimeError("submitter stopped early")
                     check_time()
                     time.sleep(0.0002)
-                outs[i] = srv.wait(tickets[i], timeout_s=max(1.0, time_limit_s - (time.perf_counter() - t_start)))
-                if outs[i] is None:
+                out = srv.wait(tickets[i], timeout_s=max(1.0, time_limit_s - (time.perf_counter() - t_start)))
+                if out is None:
                     raise TimeoutError("request did not finish")
+                done[i] = time.perf_counter() - t0
+                outs[i] = out
+
+            th = threading.Thread(target=submitter, daemon=True)
+            th.start()
+            with ThreadPoolExecutor(max_workers=min(m, 64)) as ex:
+                for f in [ex.submit(waiter, i) for i in range(m)]:
+                    f.result()
             th.join()
             st = srv.stats()
-        return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "graphs_per_s": st["graphs_per_s"]}, outs
+        lat = [(done[i] - arrivals[i]) * 1e3 for i in range(m)]
+        return {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "graphs_per_s": m / max(done),
+                "server_internal": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                                    "latency": "apsp_submit return -> result in pinned host memory"}}, outs
 
     def run_plain(arrivals):
         lat, outs = [], []
@@ -354,7 +371,7 @@ def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), 
                         "0.05-0.5, weights [1,1000]), half complete fp32 (weights (0,1])",
             "saturation": {"server": sat, "plain": base},
             "sweep": sweep, "same_results_as_plain": exact,
-            "latency": "submit (arrival) -> result in host memory"}
+            "latency": "scheduled arrival -> result in the caller's host array (client clock, both paths)"}
 
 
 def run_reference(a):
@@ -483,11 +500,13 @@ def run_ours(a):
     peaks, peak_kind = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # Min-plus ALU roofline.  The minimum runs on the ALU pipe: 16 lanes per
-    # SM sub-partition, 64 per SM per clock.  int32: one DPX add-min per
-    # relaxation -> 64 relaxations/clock/SM.  fp32: one three-input min folds
-    # two candidates (after one packed f32x2 add) -> 128 relaxations/clock/SM.
-    lanes = 64 if a.dtype == "i32" else 128  # int16x2: two relaxations per DPX lane
+    # Min-plus ALU roofline.  Every candidate d_ik + d_kj needs one 32-bit
+    # minimum, and minima run on the ALU pipe: 16 lanes per SM sub-partition,
+    # 64 per SM per clock.  int32 and fp32: 64 relaxations/clock/SM (a
+    # three-input min folds two candidates but retires them at the same rate,
+    # measured: forms 4 and 5 of apsp_ubench_minplus); int16x2: two
+    # relaxations per DPX lane, 128/clock/SM.
+    lanes = 128 if a.dtype == "i16" else 64
     peak = sms * sm_max * 1e6 * lanes
     # the same instruction form in isolation (phase-3 inner loop on shared-
     # memory operands, every SM): the sustained ceiling of the form
@@ -512,7 +531,7 @@ def run_ours(a):
                      "achieved": achieved, "peak": peak,
                      "unit": "relaxations/s", "frac": achieved / peak,
                      "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz ({peak_kind} max clock) x {lanes} relaxations "
-                                   "per clock per SM (64 ALU-pipe lanes; fp32: 2 per three-input min; "
+                                   "per clock per SM (one 32-bit min per candidate on 64 ALU-pipe lanes; "
                                    "int16x2: 2 per DPX lane)",
                      "form_ceiling": form_ceiling, "frac_of_form_ceiling": achieved / form_ceiling,
                      "traffic": _measured_traffic(a.dtype, n, cfg.kblock),
