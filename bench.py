@@ -403,6 +403,16 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def _launches_per_solve(n, S, R, lookahead, dtype):
+    """Kernel launches of one solve with n a multiple of S (the benchmark
+    sizes): phase 1 and phase 2 per stage, phase 3 per stage, split into cross
+    + rest with the lookahead for every stage but the last."""
+    assert n % S == 0, "launch count derived for whole tiles only"
+    if R == 1:
+        return 1
+    return 2 * R + R + (R - 1 if lookahead else 0)
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -426,7 +436,8 @@ def run_ours(a):
     work = torch.empty_like(pristine)
     stream = torch.cuda.current_stream()
 
-    nev = 4 * R
+    E = binding.EVENTS_PER_STAGE
+    nev = E * R
     step_events = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(a.steps)]
     for evs in step_events:  # torch creates the CUDA event on its first record
         for e in evs:
@@ -455,13 +466,20 @@ def run_ours(a):
         step(step_events[k])   # per-phase events recorded on the launching stream
     t_end.record(stream)
     torch.cuda.synchronize()
-    p3_ms, p1_ms, p2_ms = [], [], []
+    S = cfg.kblock
+    p3_ms, p3_relax, p1_ms, p2_ms = [], [], [], []
     for events in step_events:
         for r in range(R):
-            p1_ms.append(events[4 * r].elapsed_time(events[4 * r + 1]))
-            p2_ms.append(events[4 * r + 1].elapsed_time(events[4 * r + 2]))
-            if R > 1 and (r + 1) * cfg.kblock <= n:   # full k-block: the TMA phase-3 kernel
-                p3_ms.append(events[4 * r + 2].elapsed_time(events[4 * r + 3]))
+            p1_ms.append(events[E * r].elapsed_time(events[E * r + 1]))
+            p2_ms.append(events[E * r + 1].elapsed_time(events[E * r + 2]))
+            if R > 1 and (r + 1) * S <= n:   # full k-block: the TMA phase-3 kernel
+                p3_ms.append(events[E * r + 3].elapsed_time(events[E * r + 4]))
+                # rows (= columns) the launch on the timed stream updates: all
+                # but block r, and with the lookahead also but block r+1
+                rows = n - S
+                if cfg.lookahead and r + 1 < R:
+                    rows -= min(n, (r + 2) * S) - (r + 1) * S
+                p3_relax.append(float(rows) ** 2 * S)
     torch.cuda.synchronize()
     total_ms = t_start.elapsed_time(t_end)
     clocks = sampler.stop() if sampler else None
@@ -512,10 +530,10 @@ def run_ours(a):
     # memory operands, every SM): the sustained ceiling of the form
     sink = torch.empty(sms * 2 * 256, dtype=torch.int32, device="cuda")
     form_ceiling = binding.ubench({"f32": 4, "i32": 0, "i16": 2}[a.dtype], 2000, sink)
-    p3_relax = float(cfg.phase3_relax_per_round)
     p3_mean_s = statistics.mean(p3_ms) * 1e-3 if p3_ms else float("nan")
-    achieved = p3_relax / p3_mean_s
-    hbm_bytes = 2.0 * es * (n - cfg.kblock) ** 2  # C tile read + write per phase-3 launch
+    achieved = sum(p3_relax) / (sum(p3_ms) * 1e-3) if p3_ms else float("nan")
+    p3_relax_mean = statistics.mean(p3_relax) if p3_relax else float("nan")
+    hbm_bytes = 2.0 * es * p3_relax_mean / S  # C tile read + write per phase-3 launch
     line = {
         "metric": "relaxations/s (n^3/t)", "value": value, "unit": "relaxations/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
@@ -538,9 +556,10 @@ def run_ours(a):
                      "traffic_source": "ncu dram__bytes_read+write of the same kernel at n=8192, scaled by tile count",
                      "algorithmic_hbm_GBps": hbm_bytes / p3_mean_s / 1e9,
                      "hbm_peak_GBps": peaks.get("hbm_gbs"),
-                     "phase3_ms_mean": p3_mean_s * 1e3,
+                     "phase3_ms_mean": p3_mean_s * 1e3, "phase3_relax_per_launch": p3_relax_mean,
+                     "schedule": "lookahead" if cfg.lookahead else "plain",
                      "phase1_ms_mean": statistics.mean(p1_ms), "phase2_ms_mean": statistics.mean(p2_ms)},
-        "gpu_launches": a.steps * (3 * R if R > 1 else 1),
+        "gpu_launches": a.steps * _launches_per_solve(n, S, R, cfg.lookahead, a.dtype),
         "clocks": clocks,
         "e2e": e2e,
         "paper_context": {"seconds_n16384_fp32_tesla_c1060": PAPER_SECONDS_N16384,

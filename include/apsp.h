@@ -88,19 +88,29 @@ typedef enum apsp_status {
                                      (synchronizes the stream)                           */
 #define APSP_FLAG_NO_WORKSPACE 0x10 /* use only kernels that need no device workspace
                                      (same results, slower for fp32)                     */
+#define APSP_FLAG_NO_LOOKAHEAD 0x20 /* plain stage order: phases 1 and 2 of stage b+1 do
+                                     not overlap phase 3 of stage b (same results)       */
 
 typedef struct apsp_options {
     int32_t kblock;          /* k-block depth s (64 or 128); 0 = chosen from n and dtype */
     int32_t flags;           /* APSP_FLAG_* */
     /* Optional tracing: an array of cudaEvent_t (cast to void*) of length
-       4 * rounds.  For round r the library records events[4r] before phase 1,
-       [4r+1] before phase 2, [4r+2] before phase 3 and [4r+3] after phase 3, on
-       the call's stream.  Tracing implies APSP_FLAG_NO_GRAPH.  NULL = off. */
+       5 * rounds.  For stage r the library records events[5r] before phase 1,
+       [5r+1] before phase 2, [5r+2] after phase 2, [5r+3] before and [5r+4]
+       after the phase-3 launch on the call's stream.  With the lookahead
+       schedule (apsp_config.lookahead) phases 1 and 2 of stage r > 0 run on an
+       internal stream beside phase 3 of stage r-1, so events 5r..5r+2 are
+       recorded there, and the phase-3 launch on the call's stream covers every
+       tile except row and column r+1 (those run on the internal stream
+       before phase 1 of stage r+1, untimed).  Tracing implies
+       APSP_FLAG_NO_GRAPH.  NULL = off. */
     void **events;
     int64_t n_events;
-    /* Optional device workspace of at least apsp_workspace_bytes(n, dtype,
-       kblock) bytes, 256-byte aligned, owned by the caller and used only
-       between the enqueue and the completion of this call's work on its stream.
+    /* Optional device workspace of apsp_workspace_bytes(n, dtype, kblock)
+       bytes (at least one panel buffer, half of that from 8 stages on: then
+       the plain schedule runs), 256-byte aligned, owned by the caller and used
+       only between the enqueue and the completion of this call's work on its
+       stream; smaller: APSP_EINVAL.
        NULL = the library uses a buffer of its own, one per (device, stream),
        allocated on first use (not while the stream is being captured). */
     void *workspace;
@@ -114,6 +124,9 @@ typedef struct apsp_config {
     int32_t phase3_tma;      /* 1 if the TMA-staged phase-3 kernel is used          */
     int32_t phase3_threads;  /* threads per phase-3 CTA                             */
     int64_t phase3_relax_per_round; /* relaxations phase 3 performs in a full round */
+    int32_t lookahead;       /* 1 if a call without flags uses the lookahead schedule
+                                (stages >= 8, TMA-staged kernels, library workspace) */
+    int32_t reserved;
 } apsp_config;
 
 /* Status name, e.g. "APSP_EINVAL".  Never NULL. */
@@ -172,7 +185,10 @@ APSP_API int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, voi
  * solves a copy of the current pivot column panel with every entry duplicated
  * into both halves of a 32-bit word; both are s * ceil(n/s) * s * 4 bytes
  * (8 MiB at n = 16384, s = 128), written by phase 2 and read by phase 3.
- * Without a workspace the same results come from slower phase-3 kernels.
+ * From 8 stages on, two such buffers (the lookahead schedule writes the next
+ * stage's copy while phase 3 reads the current one); a workspace holding one
+ * buffer runs the plain schedule.  Without a workspace the same results come
+ * from slower phase-3 kernels.
  */
 APSP_API int64_t apsp_workspace_bytes(int64_t n, int dtype, int32_t kblock);
 

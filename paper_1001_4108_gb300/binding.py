@@ -19,6 +19,8 @@ APSP_I32, APSP_F32, APSP_I16 = 0, 1, 2
 APSP_OK, APSP_EINVAL, APSP_ENOMEM, APSP_EUNSUPPORTED, APSP_ECUDA = 0, 1, 2, 3, 4
 APSP_ETIMEOUT, APSP_EBUSY, APSP_EPENDING, APSP_ENEGCYCLE = 5, 6, 7, 8
 FLAG_NO_GRAPH, FLAG_GENERIC, FLAG_REVERSE_K, FLAG_NEGCYCLE, FLAG_NO_WORKSPACE = 0x1, 0x2, 0x4, 0x8, 0x10
+FLAG_NO_LOOKAHEAD = 0x20
+EVENTS_PER_STAGE = 5
 INF_I32 = 1 << 29
 INF_I16 = 16383
 
@@ -39,7 +41,8 @@ class Options(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("kblock", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("phase3_tma", ctypes.c_int32), ("phase3_threads", ctypes.c_int32),
-                ("phase3_relax_per_round", ctypes.c_int64)]
+                ("phase3_relax_per_round", ctypes.c_int64), ("lookahead", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):

@@ -86,6 +86,58 @@ int run_dtype(const RunArgs &a, int dtype) {
   return APSP_EINVAL;
 }
 
+// ------------------------------------------------------- lookahead streams
+// One side stream (highest priority) and a fork / join event pair per
+// (device, launching stream), created on first use outside of stream
+// capture.  Work on one launching stream is ordered, so its solves can share
+// them; a wait always refers to a record enqueued before it, so calls from
+// several threads on one stream can only over-synchronise, never deadlock.
+struct SideEntry {
+  int dev;
+  cudaStream_t stream;
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+  int prio;
+};
+constexpr size_t kMaxSide = 32;
+std::vector<SideEntry> g_side;
+
+// Fills a->side, fork, join, side_prio (nullptr side: no lookahead).  Caller
+// holds g_mu.
+void side_resources_locked(int dev, cudaStream_t stream, bool capturing, RunArgs *a) {
+  a->side = nullptr;
+  for (auto &e : g_side)
+    if (e.dev == dev && e.stream == stream) {
+      a->side = e.side;
+      a->fork = e.fork;
+      a->join = e.join;
+      a->side_prio = e.prio;
+      return;
+    }
+  if (capturing) return;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return;
+  SideEntry e{dev, stream, nullptr, nullptr, nullptr, greatest};
+  if (cudaStreamCreateWithPriority(&e.side, cudaStreamNonBlocking, greatest) != cudaSuccess) return;
+  if (cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming) != cudaSuccess) {
+    if (e.fork) cudaEventDestroy(e.fork);
+    cudaStreamDestroy(e.side);
+    return;
+  }
+  if (g_side.size() >= kMaxSide) {  // released by CUDA once their work completes
+    cudaEventDestroy(g_side.front().fork);
+    cudaEventDestroy(g_side.front().join);
+    cudaStreamDestroy(g_side.front().side);
+    g_side.erase(g_side.begin());
+  }
+  g_side.push_back(e);
+  a->side = e.side;
+  a->fork = e.fork;
+  a->join = e.join;
+  a->side_prio = e.prio;
+}
+
 // ---------------------------------------------------------------- graphs
 // A solve is R * 3 launches.  Replaying them as one CUDA graph removes the
 // per-launch host cost, which dominates for small n.  A graph is captured the
@@ -128,6 +180,7 @@ int launch_with_graph(const RunArgs &a, int dtype, int dev) {
     return APSP_ECUDA;
   RunArgs c = a;
   c.stream = g_capture_stream[dev];
+  if (a.side) side_resources_locked(dev, c.stream, false, &c);
   if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return APSP_ECUDA;
   const int st = run_dtype(c, dtype);
   cudaGraph_t graph = nullptr;
@@ -137,7 +190,8 @@ int launch_with_graph(const RunArgs &a, int dtype, int dev) {
     return st != APSP_OK ? st : APSP_ECUDA;
   }
   cudaGraphExec_t exec = nullptr;
-  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  // keep the side stream's launch priorities in the graph
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (ie != cudaSuccess) return APSP_ECUDA;
   if (g_graphs.size() >= kMaxGraphs) {
@@ -226,11 +280,19 @@ void *library_workspace(int dev, cudaStream_t stream, size_t bytes, bool capturi
   return p;
 }
 
-size_t workspace_bytes_for(int64_t n, int dtype, int S) {
+// One panel copy (fp32 interleaved row panel, int16 replicated column panel).
+size_t panel_bytes_for(int64_t n, int dtype, int S) {
   if (n <= S) return 0;
   if (dtype == APSP_F32) return interleaved_panel_bytes(n, S);
   if (dtype == APSP_I16) return replicated_panel_bytes(n, S);
   return 0;
+}
+
+// One panel buffer, two when the lookahead schedule applies (phase 2 of the
+// next stage writes its copy while phase 3 reads the current one).
+size_t workspace_bytes_for(int64_t n, int dtype, int S) {
+  const size_t bufs = (n + S - 1) / S >= kLookaheadMinRounds ? 2 : 1;
+  return bufs * panel_bytes_for(n, dtype, S);
 }
 
 // Device buffer of apsp_fw_host, one per device, grown on demand.
@@ -282,6 +344,8 @@ extern "C" int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_conf
   cfg->phase3_threads = (S / 8) * (S / 8);
   const int64_t m = std::max<int64_t>(n - S, 0);
   cfg->phase3_relax_per_round = m * m * S;
+  cfg->lookahead = cfg->rounds >= kLookaheadMinRounds ? 1 : 0;
+  cfg->reserved = 0;
   return APSP_OK;
 }
 
@@ -313,13 +377,20 @@ extern "C" int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const ap
   const size_t need = (a.flags & APSP_FLAG_NO_WORKSPACE) ? 0 : workspace_bytes_for(n, dtype, a.S);
   if (need) {
     if (opt && opt->workspace) {
-      if (opt->workspace_bytes < (int64_t)need || reinterpret_cast<uintptr_t>(opt->workspace) % 256) return APSP_EINVAL;
+      // one panel buffer is enough (plain schedule); two allow the lookahead
+      if (opt->workspace_bytes < (int64_t)panel_bytes_for(n, dtype, a.S) ||
+          reinterpret_cast<uintptr_t>(opt->workspace) % 256)
+        return APSP_EINVAL;
       a.ws = opt->workspace;
       a.ws_bytes = (size_t)opt->workspace_bytes;
     } else {
       a.ws = library_workspace(dev, a.stream, need, cap != cudaStreamCaptureStatusNone, &a.ws_bytes);
       if (!a.ws) a.ws_bytes = 0;  // the kernels fall back to the form that needs none
     }
+  }
+  if (!(a.flags & APSP_FLAG_NO_LOOKAHEAD)) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    side_resources_locked(dev, a.stream, cap != cudaStreamCaptureStatusNone, &a);
   }
   const bool direct = (a.flags & APSP_FLAG_NO_GRAPH) || a.events || cap != cudaStreamCaptureStatusNone;
   st = direct ? run_dtype(a, dtype) : launch_with_graph(a, dtype, dev);

@@ -13,14 +13,24 @@ struct RunArgs {
   int64_t n, ld;      // vertices, leading dimension (elements)
   int S;              // tile side = k-block depth (64 or 128)
   int flags;          // APSP_FLAG_*
-  void **events;      // optional per-phase events (4 per round) or nullptr
+  void **events;      // optional per-phase events (kEventsPerStage per stage) or nullptr
   int64_t n_events;
   cudaStream_t stream;
   int *err;           // device error word
   bool tma_ok;        // layout allows the TMA-staged phase 3
   void *ws;           // device workspace (256-byte aligned) or nullptr
   size_t ws_bytes;
+  // Lookahead schedule: a second stream of higher priority (nullptr = off)
+  // and two events for the fork and join between it and `stream`.
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+  int side_prio;      // launch priority of the side-stream kernels
 };
+
+// Events a traced solve records per stage (apsp_options.events).
+constexpr int kEventsPerStage = 5;
+// Smallest tile-grid side R for which the lookahead schedule is used.
+constexpr int kLookaheadMinRounds = 8;
 
 // Workspace bytes of the packed int16x2 phase 3 (replicated column panel:
 // n_p rows x s words).

@@ -1,5 +1,7 @@
 // Host loop over the stages of Fig. 2 (one stage per k-block b): phase 1,
-// phase 2 and phase 3 are three stream-ordered launches, as in Sec. 3.2.
+// phase 2 and phase 3 are stream-ordered launches, as in Sec. 3.2, with an
+// optional lookahead that overlaps the next stage's phases 1 and 2 with the
+// bulk of phase 3.
 #pragma once
 
 #include "../../include/apsp.h"
@@ -81,6 +83,7 @@ static bool make_interleaved_map(float *bp, int64_t np, CUtensorMap *m) {
 template <typename T, int S>
 struct Kernels {
   static constexpr int NT1 = (S / 4) * (S / 4);
+  static constexpr int NT1_SIDE = (S / 8) * (S / 4);  // phase 1 beside phase 3
   static constexpr int NT2 = S == 64 ? 256 : 1024;
   using C = typename Arith<T>::C;
   static constexpr size_t SM2 = 2 * (size_t)S * S * sizeof(C);
@@ -97,6 +100,45 @@ struct Kernels {
   }
 };
 
+// Launches `k` on `st`; prio != 0 sets the launch's scheduling priority
+// (recorded in the node when the stream is being captured).
+template <typename... KP, typename... Args>
+static cudaError_t launch(void (*k)(KP...), dim3 grid, int threads, size_t smem, cudaStream_t st, int prio,
+                          Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  if (prio != 0) {
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// The stages of Fig. 2 for one matrix.
+//
+// Plain schedule, per stage b on the caller's stream: phase 1, phase 2,
+// phase 3 (all doubly dependent tiles).
+//
+// Lookahead schedule (R >= kLookaheadMinRounds, TMA kernels, a side stream):
+// phase 3 of stage b is split into cross(b) -- row and column b+1, the tiles
+// that phases 1 and 2 of stage b+1 read -- and rest(b), every other tile.
+//   side stream:    cross(b), phase 1 (b+1), phase 2 (b+1)
+//   caller's stream: rest(b)
+// both starting once phase 2 (b) and rest(b-1) are done, and joined before
+// stage b+1 continues.  rest(b) reads panel b and writes no tile of row or
+// column b+1, which phase 2 (b+1) updates beside it; the panel copies that
+// phase 2 writes for phase 3 (interleaved fp32 row panel, replicated int16
+// column panel) alternate between two workspace buffers.  The side stream's
+// launches run at a higher priority, so their CTAs take SM slots as rest(b)
+// CTAs retire: the mostly serial phase 1 and the one-wave phase 2 no longer
+// leave the GPU idle between the phase-3 launches.  Every tile still sees
+// every stage in order, so results equal the plain schedule's bit for bit.
 template <typename T, int S, bool HAS_TMA>
 static int run_rounds(const RunArgs &a) {
   using K = Kernels<T, S>;
@@ -133,109 +175,162 @@ static int run_rounds(const RunArgs &a) {
   T *d = static_cast<T *>(a.d);
   const int64_t n = a.n, ld = a.ld;
   const int R = (int)((n + S - 1) / S);
+  const bool ragged = (n % S) != 0;
   const int reverse = (a.flags & APSP_FLAG_REVERSE_K) ? 1 : 0;
   const bool generic_only = (a.flags & APSP_FLAG_GENERIC) != 0;
-  cudaStream_t st = a.stream;
-
-  CUtensorMap mA, mB, mBp;
-  bool use_tma = false, use_packed = false;
-  T *bp = nullptr;
+  const cudaStream_t st = a.stream;
   const int64_t np = (int64_t)R * S;
+
+  // Tensor maps; the panel copies of phase 2 (one buffer, or two for the
+  // lookahead schedule).
+  CUtensorMap mA, mB, mBp[2];
+  bool use_tma = false, use_packed = false;
+  T *bp[2] = {nullptr, nullptr};
+  int nbuf = 0;
   if constexpr (HAS_TMA) {
     use_tma = a.tma_ok && !generic_only && R > 1 && make_panel_maps<T, S>(d, n, ld, &mA, &mB);
     if constexpr (std::is_same<T, float>::value) {
-      use_packed = use_tma && a.ws && a.ws_bytes >= interleaved_panel_bytes(n, S) &&
-                   reinterpret_cast<uintptr_t>(a.ws) % 256 == 0 &&
-                   make_interleaved_map<S>(static_cast<float *>(a.ws), np, &mBp);
-      if (use_packed) bp = static_cast<T *>(a.ws);
+      const size_t pb = interleaved_panel_bytes(n, S);
+      if (use_tma && a.ws && a.ws_bytes >= pb && reinterpret_cast<uintptr_t>(a.ws) % 256 == 0) {
+        nbuf = a.ws_bytes >= 2 * pb ? 2 : 1;
+        use_packed = true;
+        for (int i = 0; i < nbuf; ++i) {
+          bp[i] = reinterpret_cast<T *>(static_cast<char *>(a.ws) + i * pb);
+          use_packed = use_packed && make_interleaved_map<S>(reinterpret_cast<float *>(bp[i]), np, &mBp[i]);
+        }
+        if (!use_packed) nbuf = 0;
+      }
     }
   }
 
-  CUtensorMap mA16, mB16, mArep;
+  CUtensorMap mA16, mB16, mArep[2];
   bool use_s16 = false;
-  uint32_t *arep = nullptr;
+  uint32_t *arep[2] = {nullptr, nullptr};
   if constexpr (std::is_same<T, int16_t>::value) {
-    arep = static_cast<uint32_t *>(a.ws);
-    use_s16 = a.tma_ok && !generic_only && R > 1 && a.ws && a.ws_bytes >= replicated_panel_bytes(n, S) &&
-              reinterpret_cast<uintptr_t>(a.ws) % 256 == 0 &&
-              make_s16_maps<S>(reinterpret_cast<int16_t *>(d), n, ld, arep, np, &mA16, &mB16, &mArep);
+    const size_t pb = replicated_panel_bytes(n, S);
+    if (a.tma_ok && !generic_only && R > 1 && a.ws && a.ws_bytes >= pb &&
+        reinterpret_cast<uintptr_t>(a.ws) % 256 == 0) {
+      nbuf = a.ws_bytes >= 2 * pb ? 2 : 1;
+      use_s16 = true;
+      for (int i = 0; i < nbuf; ++i) {
+        arep[i] = reinterpret_cast<uint32_t *>(static_cast<char *>(a.ws) + i * pb);
+        use_s16 = use_s16 && make_s16_maps<S>(reinterpret_cast<int16_t *>(d), n, ld, arep[i], np, &mA16, &mB16,
+                                              &mArep[i]);
+      }
+      if (!use_s16) nbuf = 0;
+    }
   }
 
-  auto ev = [&](int64_t idx) -> bool {
-    if (!a.events || idx >= a.n_events) return true;
-    return cudaEventRecord(static_cast<cudaEvent_t>(a.events[idx]), st) == cudaSuccess;
-  };
+  // Is phase 3 of a full stage done by a TMA kernel (tile sets supported)?
+  bool p3_tma = false;
+  if constexpr (std::is_same<T, int16_t>::value) p3_tma = use_s16;
+  else p3_tma = use_tma;
+  const bool needs_panel = use_packed || use_s16;
+  const bool lookahead = p3_tma && a.side && !(a.flags & APSP_FLAG_NO_LOOKAHEAD) && R >= kLookaheadMinRounds &&
+                         (!needs_panel || nbuf == 2);
+  auto buf_of = [&](int b) { return lookahead ? (b & 1) : 0; };
 
-  for (int b = 0; b < R; ++b) {
-    const int last = (b == R - 1) ? 1 : 0;
-    if (!ev(4ll * b)) return APSP_ECUDA;
-    fw_phase1<T, S><<<1, K::NT1, 0, st>>>(d, n, ld, b, last);
-    if (!ev(4ll * b + 1)) return APSP_ECUDA;
-    const bool full_k = (int64_t)(b + 1) * S <= n;
-    T *bp_round = (use_packed && full_k) ? bp : nullptr;
-    if (R > 1) {
-      bool launched2 = false;
-      if constexpr (std::is_same<T, int16_t>::value) {
-        if (use_s16 && full_k) {
-          fw_tile_s16x2<S, 1><<<2 * (R - 1), P3S16<S>::TPB, P3S16<S>::SMEM, st>>>(
-              mA16, mB16, reinterpret_cast<int16_t *>(d), n, ld, b, R, reverse, arep, a.err);
-          launched2 = true;
-        }
-      }
-      if constexpr (HAS_TMA) {
-        if (use_tma && full_k) {
-          fw_tile_tma<T, S, 1><<<2 * (R - 1), P3Tma<S>::TPB, P3Tma<S>::SMEM, st>>>(
-              mA, mB, d, n, ld, b, R, last, reverse, bp_round, 2 * np, a.err);
-          launched2 = true;
-        }
-      }
-      if (!launched2)
-        fw_phase2<T, S, K::NT2><<<2 * (R - 1), K::NT2, K::SM2, st>>>(d, n, ld, b, R, last, bp_round, 2 * np);
+  auto ev = [&](int64_t idx, cudaStream_t s) -> bool {
+    if (!a.events || idx >= a.n_events) return true;
+    return cudaEventRecord(static_cast<cudaEvent_t>(a.events[idx]), s) == cudaSuccess;
+  };
+  auto full_k = [&](int b) { return (int64_t)(b + 1) * S <= n; };
+
+  // ---- the three phases of one stage, on stream s with priority prio
+  auto phase1 = [&](int b, cudaStream_t s, int prio) -> cudaError_t {
+    const int last = b == R - 1 ? 1 : 0;
+    if (prio != 0) return launch(fw_phase1_side<T, S>, dim3(1), K::NT1_SIDE, 0, s, prio, d, n, ld, b, last);
+    return launch(fw_phase1<T, S>, dim3(1), K::NT1, 0, s, 0, d, n, ld, b, last);
+  };
+  auto phase2 = [&](int b, cudaStream_t s, int prio) -> cudaError_t {
+    if (R == 1) return cudaSuccess;
+    const int last = b == R - 1 ? 1 : 0;
+    const dim3 g(2 * (R - 1));
+    if constexpr (std::is_same<T, int16_t>::value) {
+      if (use_s16 && full_k(b))
+        return launch(fw_tile_s16x2<S, 1>, g, P3S16<S>::TPB, P3S16<S>::SMEM, s, prio, mA16, mB16,
+                      reinterpret_cast<int16_t *>(d), n, ld, b, R, TileSet{}, reverse, arep[buf_of(b)], a.err);
     }
-    if (!ev(4ll * b + 2)) return APSP_ECUDA;
-    if (R > 1) {
-      const dim3 grid(R - 1, R - 1);
-      bool launched = false;
+    T *bpb = (use_packed && full_k(b)) ? bp[buf_of(b)] : nullptr;
+    if constexpr (HAS_TMA) {
+      if (use_tma && full_k(b))
+        return launch(fw_tile_tma<T, S, 1>, g, P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB, d, n, ld, b, R,
+                      TileSet{}, last, reverse, bpb, 2 * np, a.err);
+    }
+    return launch(fw_phase2<T, S, K::NT2>, g, K::NT2, K::SM2, s, prio, d, n, ld, b, R, last, bpb, 2 * np);
+  };
+  // phase 3 of stage b over the tiles of `kind`
+  auto phase3 = [&](int b, int kind, cudaStream_t s, int prio) -> cudaError_t {
+    if (R == 1) return cudaSuccess;
+    const int last = b == R - 1 ? 1 : 0;
+    if (full_k(b)) {
       if constexpr (std::is_same<T, int16_t>::value) {
-        if (use_s16 && full_k) {
-          fw_tile_s16x2<S, 0><<<grid, P3S16<S>::TPB, P3S16<S>::SMEM, st>>>(
-              mArep, mB16, reinterpret_cast<int16_t *>(d), n, ld, b, R, reverse, arep, a.err);
-          launched = true;
+        if (use_s16) {
+          const TileSet ts = make_tileset(kind, kPartAny, b, R, ragged);
+          if (ts.total() == 0) return cudaSuccess;
+          return launch(fw_tile_s16x2<S, 0>, dim3(ts.total()), P3S16<S>::TPB, P3S16<S>::SMEM, s, prio,
+                        mArep[buf_of(b)], mB16, reinterpret_cast<int16_t *>(d), n, ld, b, R, ts, reverse,
+                        arep[buf_of(b)], a.err);
         }
       }
       if constexpr (std::is_same<T, float>::value) {
-        if (bp_round) {
-          // interior tiles (all rows/columns inside the matrix), then the
-          // edge tiles of a ragged matrix
-          const int ragged = (n % S) != 0 ? 1 : 0;
-          const dim3 gi(R - 1 - ragged, R - 1 - ragged);
-          const int ne = ragged ? 2 * R - 3 : 0;
+        if (use_packed) {
           const int tpb = P3Tma<S>::TPB, sm = P3Tma<S>::SMEM;
-          if (gi.x > 0) {
-            if (reverse)
-              fw_phase3_f32x2<S, true, true><<<gi, tpb, sm, st>>>(mA, mBp, d, n, ld, b, R, a.err);
-            else
-              fw_phase3_f32x2<S, false, true><<<gi, tpb, sm, st>>>(mA, mBp, d, n, ld, b, R, a.err);
-          }
-          if (ne > 0) {
-            if (reverse)
-              fw_phase3_f32x2<S, true, false><<<ne, tpb, sm, st>>>(mA, mBp, d, n, ld, b, R, a.err);
-            else
-              fw_phase3_f32x2<S, false, false><<<ne, tpb, sm, st>>>(mA, mBp, d, n, ld, b, R, a.err);
-          }
-          launched = true;
+          const CUtensorMap &mb = mBp[buf_of(b)];
+          const TileSet ti = make_tileset(kind, kPartInterior, b, R, ragged);
+          const TileSet te = make_tileset(kind, kPartEdge, b, R, ragged);
+          cudaError_t e = cudaSuccess;
+          if (ti.total() > 0)
+            e = reverse ? launch(fw_phase3_f32x2<S, true, true>, dim3(ti.total()), tpb, sm, s, prio, mA, mb, d,
+                                 n, ld, b, ti, a.err)
+                        : launch(fw_phase3_f32x2<S, false, true>, dim3(ti.total()), tpb, sm, s, prio, mA, mb, d,
+                                 n, ld, b, ti, a.err);
+          if (e == cudaSuccess && te.total() > 0)
+            e = reverse ? launch(fw_phase3_f32x2<S, true, false>, dim3(te.total()), tpb, sm, s, prio, mA, mb, d,
+                                 n, ld, b, te, a.err)
+                        : launch(fw_phase3_f32x2<S, false, false>, dim3(te.total()), tpb, sm, s, prio, mA, mb, d,
+                                 n, ld, b, te, a.err);
+          return e;
         }
       }
       if constexpr (HAS_TMA) {
-        if (!launched && use_tma && full_k) {
-          fw_tile_tma<T, S, 0><<<grid, P3Tma<S>::TPB, P3Tma<S>::SMEM, st>>>(mA, mB, d, n, ld, b, R, last, reverse,
-                                                                            (T *)nullptr, 0, a.err);
-          launched = true;
+        if (use_tma) {
+          const TileSet ts = make_tileset(kind, kPartAny, b, R, ragged);
+          if (ts.total() == 0) return cudaSuccess;
+          return launch(fw_tile_tma<T, S, 0>, dim3(ts.total()), P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB, d,
+                        n, ld, b, R, ts, last, reverse, (T *)nullptr, (int64_t)0, a.err);
         }
       }
-      if (!launched) fw_phase3_generic<T, S><<<grid, 256, K::SM3G, st>>>(d, n, ld, b, last, reverse);
     }
-    if (!ev(4ll * b + 3)) return APSP_ECUDA;
+    // generic kernel: all tiles of the stage (plain schedule only)
+    return launch(fw_phase3_generic<T, S>, dim3(R - 1, R - 1), 256, K::SM3G, s, prio, d, n, ld, b, last,
+                  reverse);
+  };
+
+  const int E = kEventsPerStage;
+  auto stage_12 = [&](int b, cudaStream_t s, int prio) -> bool {
+    return ev((int64_t)E * b, s) && phase1(b, s, prio) == cudaSuccess && ev((int64_t)E * b + 1, s) &&
+           phase2(b, s, prio) == cudaSuccess && ev((int64_t)E * b + 2, s);
+  };
+
+  if (!stage_12(0, st, 0)) return APSP_ECUDA;
+  for (int b = 0; b < R; ++b) {
+    if (lookahead && b + 1 < R) {
+      // b + 1 < R implies a full k-block for stage b
+      if (cudaEventRecord(a.fork, st) != cudaSuccess || cudaStreamWaitEvent(a.side, a.fork, 0) != cudaSuccess)
+        return APSP_ECUDA;
+      if (phase3(b, kTilesCross, a.side, a.side_prio) != cudaSuccess) return APSP_ECUDA;
+      if (!stage_12(b + 1, a.side, a.side_prio)) return APSP_ECUDA;
+      if (cudaEventRecord(a.join, a.side) != cudaSuccess) return APSP_ECUDA;
+      if (!ev((int64_t)E * b + 3, st) || phase3(b, kTilesRest, st, 0) != cudaSuccess ||
+          !ev((int64_t)E * b + 4, st))
+        return APSP_ECUDA;
+      if (cudaStreamWaitEvent(st, a.join, 0) != cudaSuccess) return APSP_ECUDA;
+    } else {
+      if (!ev((int64_t)E * b + 3, st) || phase3(b, kTilesAll, st, 0) != cudaSuccess || !ev((int64_t)E * b + 4, st))
+        return APSP_ECUDA;
+      if (b + 1 < R && !stage_12(b + 1, st, 0)) return APSP_ECUDA;
+    }
     if (cudaPeekAtLastError() != cudaSuccess) return APSP_ECUDA;
   }
   return APSP_OK;

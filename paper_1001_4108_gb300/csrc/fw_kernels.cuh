@@ -18,6 +18,7 @@
 #pragma once
 
 #include "apsp_common.cuh"
+#include "tileset.h"
 
 #include <type_traits>
 
@@ -26,72 +27,88 @@ namespace apsp {
 // ------------------------------------------------------------------ phase 1
 // One CTA closes the diagonal tile (b, b): s sequential k steps, each a rank-1
 // update x_ij <- min(x_ij, x_ik + x_kj) of the whole tile.
-// The tile lives in registers, a 4 x 4 block per thread ((s/4)^2 threads);
-// only row k and column k travel through shared memory.  Within step k, row k
-// and column k do not change (d_kk >= 0), so the owners of row/column k+1
-// publish them right after their own step-k update, into the other half of a
-// double buffer: one barrier per step.
-template <typename T, int S>
-__global__ void __launch_bounds__((S / 4) * (S / 4)) fw_phase1(T *__restrict__ d, int64_t n, int64_t ld, int b,
-                                                               int last) {
+// The tile lives in registers, an MR x MC block per thread ((s/MR)(s/MC)
+// threads); only row k and column k travel through shared memory.  Within
+// step k, row k and column k do not change (d_kk >= 0), so the owners of
+// row/column k+1 publish them right after their own step-k update, into the
+// other half of a double buffer: one barrier per step.
+template <typename T, int S, int MR, int MC>
+__device__ __forceinline__ void phase1_body(T *__restrict__ d, int64_t n, int64_t ld, int b, int last) {
   using C = typename Arith<T>::C;
-  constexpr int Q = S / 4;  // threads per dimension
+  constexpr int QC = S / MC;  // thread columns
+  constexpr int U = MR > MC ? MR : MC;  // k steps per unrolled group (MR, MC in {4, 8})
   __shared__ __align__(16) C rowbuf[2][S];
   __shared__ __align__(16) C colbuf[2][S];
-  const int tx = threadIdx.x % Q, ty = threadIdx.x / Q;
+  const int tx = threadIdx.x % QC, ty = threadIdx.x / QC;
   const int64_t base = (int64_t)b * S;
-  C x[4][4];
+  C x[MR][MC];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < MR; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int64_t gi = base + 4 * ty + a, gj = base + 4 * tx + c;
+    for (int c = 0; c < MC; ++c) {
+      const int64_t gi = base + MR * ty + a, gj = base + MC * tx + c;
       x[a][c] = (gi < n && gj < n) ? Arith<T>::load(d[gi * ld + gj]) : Arith<T>::inf();
     }
   if (ty == 0) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) rowbuf[0][4 * tx + c] = x[0][c];
+    for (int c = 0; c < MC; ++c) rowbuf[0][MC * tx + c] = x[0][c];
   }
   if (tx == 0) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) colbuf[0][4 * ty + a] = x[a][0];
+    for (int a = 0; a < MR; ++a) colbuf[0][MR * ty + a] = x[a][0];
   }
-  for (int kq = 0; kq < Q; ++kq) {
+  for (int kq = 0; kq < S / U; ++kq) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int k = 4 * kq + u;
+    for (int u = 0; u < U; ++u) {
+      const int k = U * kq + u;
       __syncthreads();
-      C rk[4], ck[4];
+      C rk[MC], ck[MR];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) rk[c] = rowbuf[k & 1][4 * tx + c];
+      for (int c = 0; c < MC; ++c) rk[c] = rowbuf[k & 1][MC * tx + c];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) ck[a] = colbuf[k & 1][4 * ty + a];
+      for (int a = 0; a < MR; ++a) ck[a] = colbuf[k & 1][MR * ty + a];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < MR; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) x[a][c] = Arith<T>::relax(x[a][c], ck[a], rk[c]);
-      // publish row / column k + 1 (local index (u + 1) % 4 of its owners)
+        for (int c = 0; c < MC; ++c) x[a][c] = Arith<T>::relax(x[a][c], ck[a], rk[c]);
+      // publish row k + 1 (local row (u + 1) % MR of thread row (k + 1) / MR)
+      // and column k + 1 (local column (u + 1) % MC of thread column (k + 1) / MC)
       const int k1 = k + 1;
       if (k1 < S) {
-        const int owner = k1 >> 2;
-        if (ty == owner) {
+        if (ty == k1 / MR) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) rowbuf[k1 & 1][4 * tx + c] = x[(u + 1) & 3][c];
+          for (int c = 0; c < MC; ++c) rowbuf[k1 & 1][MC * tx + c] = x[(u + 1) % MR][c];
         }
-        if (tx == owner) {
+        if (tx == k1 / MC) {
 #pragma unroll
-          for (int a = 0; a < 4; ++a) colbuf[k1 & 1][4 * ty + a] = x[a][(u + 1) & 3];
+          for (int a = 0; a < MR; ++a) colbuf[k1 & 1][MR * ty + a] = x[a][(u + 1) % MC];
         }
       }
     }
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < MR; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int64_t gi = base + 4 * ty + a, gj = base + 4 * tx + c;
+    for (int c = 0; c < MC; ++c) {
+      const int64_t gi = base + MR * ty + a, gj = base + MC * tx + c;
       if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(x[a][c]) : (T)x[a][c];
     }
+}
+
+// Alone on the GPU: 4 x 4 blocks, the most threads (latency bound).
+template <typename T, int S>
+__global__ void __launch_bounds__((S / 4) * (S / 4)) fw_phase1(T *__restrict__ d, int64_t n, int64_t ld, int b,
+                                                               int last) {
+  phase1_body<T, S, 4, 4>(d, n, ld, b, last);
+}
+
+// Beside phase 3 (lookahead schedule): 8 x 4 blocks and at most 64 registers
+// per thread, so that the CTA fits on an SM next to a phase-3 CTA
+// (S = 128: 512 threads x 64 registers = 32768).
+template <typename T, int S>
+__global__ void __launch_bounds__((S / 8) * (S / 4), S == 128 ? 2 : 4)
+    fw_phase1_side(T *__restrict__ d, int64_t n, int64_t ld, int b, int last) {
+  phase1_body<T, S, 8, 4>(d, n, ld, b, last);
 }
 
 // ------------------------------------------------------------------ phase 2
@@ -229,8 +246,9 @@ __global__ void __launch_bounds__(256) fw_phase3_generic(T *__restrict__ d, int6
 //     a = tile (I, b) of the matrix, b = tile (b, J) of the matrix,
 // for 4-byte element types, a full k-block (k0 + S <= n) and 16-byte aligned
 // rows.
-//   phase 3 (MODE 0): the doubly dependent tiles I != b, J != b; grid
-//            (R-1, R-1).  Their operands are final for the stage.
+//   phase 3 (MODE 0): doubly dependent tiles I != b, J != b, those of the
+//            tile set `ts`, one per CTA.  Their operands are final for the
+//            stage.
 //   phase 2 (MODE 1): the singly dependent tiles; blockIdx.x < R-1 takes the
 //            row panel tile (b, J), the rest the column panel tile (I, b).
 //            After phase 1 the diagonal tile D is closed (its own shortest
@@ -315,7 +333,7 @@ __device__ __forceinline__ void lds4(const T *p, T &x0, T &x1, T &x2, T &x3) {
 template <typename T, int S, int MODE>
 __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     fw_tile_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                T *__restrict__ d, int64_t n, int64_t ld, int b, int R, int last, int reverse,
+                T *__restrict__ d, int64_t n, int64_t ld, int b, int R, const TileSet ts, int last, int reverse,
                 T *__restrict__ bp, int64_t bp_ld, int *err) {
   using P = P3Tma<S>;
   constexpr int G = P::G;
@@ -327,19 +345,19 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
   T *Bs = reinterpret_cast<T *>(base + P::STAGES * P::A_BYTES);
   uint64_t *full = reinterpret_cast<uint64_t *>(base + P::STAGES * (P::A_BYTES + P::B_BYTES));
 
+  int *tile_ij = reinterpret_cast<int *>(full + P::STAGES);  // (It, Jt), reread after the main loop
+
   const int tid = threadIdx.x;
   const int tx = tid % G, ty = tid / G;
   int It, Jt;
-  bool row_panel = false;
   if (MODE == 0) {
-    It = skip_pivot(blockIdx.y, b);
-    Jt = skip_pivot(blockIdx.x, b);
+    ts.tile(blockIdx.x, It, Jt);
   } else {
-    row_panel = (int)blockIdx.x < R - 1;
-    It = row_panel ? b : skip_pivot(blockIdx.x - (R - 1), b);
-    Jt = row_panel ? skip_pivot(blockIdx.x, b) : b;
+    const bool rp = (int)blockIdx.x < R - 1;
+    It = rp ? b : skip_pivot(blockIdx.x - (R - 1), b);
+    Jt = rp ? skip_pivot(blockIdx.x, b) : b;
   }
-  const int64_t I0 = (int64_t)It * S, J0 = (int64_t)Jt * S;
+  int64_t I0 = (int64_t)It * S, J0 = (int64_t)Jt * S;
   const int k0 = b * S;
 
   if (tid == 0) {
@@ -348,6 +366,8 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
 #pragma unroll
     for (int s = 0; s < P::STAGES; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
+    tile_ij[0] = It;
+    tile_ij[1] = Jt;
   }
   __syncthreads();
   if (tid == 0) {
@@ -442,12 +462,19 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     if (tid == 0 && s + P::STAGES < P::NSL) {
       const int s2 = s + P::STAGES;
       mbar_arrive_expect_tx(&full[st], P::A_BYTES + P::B_BYTES);
-      tma_load_2d(As + st * (S * KS), &tmA, &full[st], k0 + s2 * KS, (int)I0);
-      tma_load_2d(Bs + st * (KS * S), &tmB, &full[st], (int)J0, k0 + s2 * KS);
+      tma_load_2d(As + st * (S * KS), &tmA, &full[st], k0 + s2 * KS, lds_volatile(tile_ij) * S);
+      tma_load_2d(Bs + st * (KS * S), &tmB, &full[st], lds_volatile(tile_ij + 1) * S, k0 + s2 * KS);
     }
   }
 
-  if (full_tile) {
+  // tile coordinates from shared memory: nothing of them stays live in
+  // registers across the main loop
+  It = lds_volatile(tile_ij);
+  Jt = lds_volatile(tile_ij + 1);
+  I0 = (int64_t)It * S;
+  J0 = (int64_t)Jt * S;
+  const bool row_panel = MODE == 1 && It == b;
+  if (I0 + S <= n && J0 + S <= n) {
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       T *row = d + (I0 + ty + G * r) * ld + J0 + 4 * tx;
@@ -493,9 +520,9 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
 // load yields the (k, k+1) pairs of two adjacent columns.  Thread columns:
 // j = 2 (tx + G m) + e, m < 4, e < 2.
 //
-// FULL = true: every row and column of the tile is inside the matrix (the
-// interior tiles); FULL = false: masked loads/stores, blockIdx.x enumerates
-// the edge tiles (last tile row, then last tile column) of a ragged matrix.
+// blockIdx.x numbers the tiles of the launch's tile set.  FULL = true: every
+// row and column of every tile is inside the matrix (interior tiles); FULL =
+// false: masked loads/stores (the edge tiles of a ragged matrix).
 __device__ __forceinline__ float min3f(float a, float b, float c) {
   float r;
   asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -505,33 +532,10 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 // (a.x + b.x, a.y + b.y), each rounded to nearest: one packed add.f32x2.
 __device__ __forceinline__ float2 add2f(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
-// Tile (I, J) of a phase-3 CTA.  Interior launches use blockIdx directly;
-// edge launches number the ragged last tile row (x = 0..R-2) and then the
-// last tile column (y = 0..R-3) in blockIdx.x.
-template <bool FULL>
-__device__ __forceinline__ void phase3_tile(int b, int R, int &It, int &Jt) {
-  int bx, by;
-  if (FULL) {
-    bx = blockIdx.x;
-    by = blockIdx.y;
-  } else {
-    const int t = blockIdx.x;
-    if (t < R - 1) {
-      by = R - 2;
-      bx = t;
-    } else {
-      bx = R - 2;
-      by = t - (R - 1);
-    }
-  }
-  It = skip_pivot(by, b);
-  Jt = skip_pivot(bx, b);
-}
-
 template <int S, bool REVERSE, bool FULL>
 __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     fw_phase3_f32x2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBp,
-                    float *__restrict__ d, int64_t n, int64_t ld, int b, int R, int *err) {
+                    float *__restrict__ d, int64_t n, int64_t ld, int b, const TileSet ts, int *err) {
   using P = P3Tma<S>;
   constexpr int G = P::G;
   constexpr int KS = P::KS;
@@ -546,7 +550,7 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
   const int tid = threadIdx.x;
   const int tx = tid % G, ty = tid / G;
   int It, Jt;
-  phase3_tile<FULL>(b, R, It, Jt);
+  ts.tile(blockIdx.x, It, Jt);
   const int k0 = b * S;
 
   if (tid == 0) {
@@ -697,7 +701,7 @@ __device__ __forceinline__ uint32_t rep_hi(uint32_t w) { return __byte_perm(w, 0
 template <int S, int MODE>
 __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
     fw_tile_s16x2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  int16_t *__restrict__ d, int64_t n, int64_t ld, int b, int R, int reverse,
+                  int16_t *__restrict__ d, int64_t n, int64_t ld, int b, int R, const TileSet ts, int reverse,
                   uint32_t *__restrict__ arep, int *err) {
   using P = P3S16<S>;
   constexpr int G = P::G;
@@ -710,20 +714,19 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
   unsigned char *Bs = base + P::STAGES * A_BYTES;
   uint64_t *full = reinterpret_cast<uint64_t *>(base + P::STAGES * (A_BYTES + P::B_BYTES));
 
+  int *tile_ij = reinterpret_cast<int *>(full + P::STAGES);  // (It, Jt), reread after the main loop
+
   const int tid = threadIdx.x;
   const int tx = tid % G, ty = tid / G;
   int It, Jt;
-  bool col_panel = false;
   if (MODE == 0) {
-    It = skip_pivot(blockIdx.y, b);
-    Jt = skip_pivot(blockIdx.x, b);
+    ts.tile(blockIdx.x, It, Jt);
   } else {
-    const bool row_panel = (int)blockIdx.x < R - 1;
-    col_panel = !row_panel;
-    It = row_panel ? b : skip_pivot(blockIdx.x - (R - 1), b);
-    Jt = row_panel ? skip_pivot(blockIdx.x, b) : b;
+    const bool rp = (int)blockIdx.x < R - 1;
+    It = rp ? b : skip_pivot(blockIdx.x - (R - 1), b);
+    Jt = rp ? skip_pivot(blockIdx.x, b) : b;
   }
-  const int64_t I0 = (int64_t)It * S, J0 = (int64_t)Jt * S;
+  int64_t I0 = (int64_t)It * S, J0 = (int64_t)Jt * S;
   const int k0 = b * S;
 
   if (tid == 0) {
@@ -732,15 +735,18 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
 #pragma unroll
     for (int s = 0; s < P::STAGES; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
+    tile_ij[0] = It;
+    tile_ij[1] = Jt;
   }
   __syncthreads();
   auto issue = [&](int s, int st) {
+    const int i0 = lds_volatile(tile_ij) * S, j0 = lds_volatile(tile_ij + 1) * S;
     mbar_arrive_expect_tx(&full[st], A_BYTES + P::B_BYTES);
     if (MODE == 0)
-      tma_load_2d(As + st * A_BYTES, &tmA, &full[st], s * KS, (int)I0);  // workspace: x = k within block
+      tma_load_2d(As + st * A_BYTES, &tmA, &full[st], s * KS, i0);  // workspace: x = k within block
     else
-      tma_load_2d(As + st * A_BYTES, &tmA, &full[st], k0 + s * KS, (int)I0);
-    tma_load_2d(Bs + st * P::B_BYTES, &tmB, &full[st], (int)J0, k0 + s * KS);
+      tma_load_2d(As + st * A_BYTES, &tmA, &full[st], k0 + s * KS, i0);
+    tma_load_2d(Bs + st * P::B_BYTES, &tmB, &full[st], j0, k0 + s * KS);
   };
   if (tid == 0) {
 #pragma unroll
@@ -811,11 +817,19 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
     if (tid == 0 && s + P::STAGES < P::NSL) issue(s + P::STAGES, st);
   }
 
+  // tile coordinates from shared memory: nothing of them stays live in
+  // registers across the main loop
+  It = lds_volatile(tile_ij);
+  Jt = lds_volatile(tile_ij + 1);
+  I0 = (int64_t)It * S;
+  J0 = (int64_t)Jt * S;
+  const bool full_tile_out = I0 + S <= n && J0 + S <= n;
+  const bool col_panel = MODE == 1 && It != b;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int64_t gi = I0 + ty + G * r;
     const int64_t gj = J0 + 8 * tx;
-    if (full_tile) {
+    if (full_tile_out) {
       *reinterpret_cast<uint4 *>(d + gi * ld + gj) = make_uint4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
     } else {
 #pragma unroll

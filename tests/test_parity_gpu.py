@@ -117,13 +117,15 @@ def test_fp32_user_workspace():
     n = 900
     w, _ = inputs.dense_f32(n, seed=5, reweighted=True)
     nbytes = binding.workspace_bytes(n, binding.APSP_F32)
-    assert nbytes == 64 * 960 * 4
-    ws = torch.full((nbytes // 4,), float("nan"), device="cuda")
-    t = torch.from_numpy(w).cuda()
-    binding.apsp_fw(t, workspace=ws)
-    torch.cuda.synchronize()
-    np.testing.assert_array_equal(t.cpu().numpy(), gpu_solve(w, flags=binding.FLAG_NO_WORKSPACE))
-    small = torch.empty(nbytes // 4 - 1, device="cuda")
+    assert nbytes == 2 * 64 * 960 * 4  # 15 stages: two panel buffers (lookahead)
+    ref = gpu_solve(w, flags=binding.FLAG_NO_WORKSPACE)
+    for size in (nbytes, nbytes // 2):  # lookahead, plain schedule
+        ws = torch.full((size // 4,), float("nan"), device="cuda")
+        t = torch.from_numpy(w).cuda()
+        binding.apsp_fw(t, workspace=ws)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(t.cpu().numpy(), ref)
+    small = torch.empty(nbytes // 8 - 1, device="cuda")
     opt = binding.Options(0, 0, None, 0, small.data_ptr(), small.numel() * 4)
     assert binding.apsp_fw_raw(t.data_ptr(), n, n, binding.APSP_F32, None, opt) == binding.APSP_EINVAL
 
@@ -152,6 +154,62 @@ def test_capture_into_user_graph():
     g.replay()
     torch.cuda.synchronize()
     np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
+
+
+# --------------------------------------------------- lookahead schedule ---
+
+def _graph(dt, n, seed):
+    if dt == "f32":
+        return inputs.dense_f32(n, seed=seed)
+    w = inputs.int_graph(n, 0.2, 0, 1000, seed=seed, potential_max=40)
+    return inputs.to_int16(w) if dt == "i16" else w
+
+
+def _oracle(dt, w):
+    return {"f32": oracle.fw_f64, "i32": oracle.fw_int32_conv, "i16": oracle.fw_int16_conv}[dt](w)
+
+
+@pytest.mark.parametrize("dt", ["f32", "i32", "i16"])
+@pytest.mark.parametrize("n,kb", [(512, 64), (1100, 64), (9 * 128 + 37, 128), (8 * 128, 128), (8 * 128 + 1, 128)])
+def test_lookahead_equals_plain(dt, n, kb):
+    # The lookahead schedule reorders independent phase-3 tiles and overlaps
+    # phases 1-2 of stage b+1 with them; results are bit-identical to the
+    # plain schedule (and, for the integers, to the oracle).  The sizes cover
+    # a ragged last stage whose row/column is the lookahead's cross.
+    w = _graph(dt, n, seed=n + kb)
+    cfg = binding.query_config(n, binding.dtype_code(w.dtype), kb)
+    assert cfg.lookahead == 1
+    a = gpu_solve(w, kblock=kb)
+    b = gpu_solve(w, kblock=kb, flags=binding.FLAG_NO_LOOKAHEAD)
+    c = gpu_solve(w, kblock=kb, flags=binding.FLAG_REVERSE_K | binding.FLAG_NO_GRAPH)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    if dt == "f32":
+        assert_fp32_close(a, oracle.fw_f64(w))
+    else:
+        np.testing.assert_array_equal(a, _oracle(dt, w))
+
+
+def test_lookahead_graph_replay_and_user_capture():
+    n = 1100
+    w = _graph("i32", n, seed=3)
+    exp = oracle.fw_int32_conv(w)
+    src = torch.from_numpy(w).cuda()
+    s = torch.cuda.Stream()
+    t = torch.empty_like(src)
+    with torch.cuda.stream(s):
+        for _ in range(3):  # direct launch (creates the side stream of s), library graph, replay
+            t.copy_(src)
+            binding.apsp_fw(t, stream=s)
+            s.synchronize()
+            np.testing.assert_array_equal(t.cpu().numpy(), exp)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):  # the user's capture takes the fork/join too
+        binding.apsp_fw(t, stream=s)
+    for _ in range(2):
+        t.copy_(src)
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(t.cpu().numpy(), exp)
 
 
 def test_negative_cycle_flag():
@@ -283,15 +341,33 @@ def test_full_size_16384_sampled(dt):
     assert (t.diagonal() == 0).all().item()
 
 
-def test_traced_events_per_phase():
-    # the tracing option records 4 events per stage on the call's stream
-    w = inputs.dense_f32(400, seed=12)
+@pytest.mark.parametrize("n,flags", [(400, 0), (1100, 0), (1100, binding.FLAG_NO_LOOKAHEAD)])
+def test_traced_events_per_phase(n, flags):
+    # the tracing option records 5 events per stage: phase 1, phase 2 (start,
+    # end) and the phase-3 launch on the call's stream (start, end)
+    E = binding.EVENTS_PER_STAGE
+    w = inputs.dense_f32(n, seed=12)
     t = torch.from_numpy(w).cuda()
-    cfg = binding.query_config(400, binding.APSP_F32)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(4 * cfg.rounds)]
+    cfg = binding.query_config(n, binding.APSP_F32)
+    lookahead = cfg.lookahead and not flags
+    assert cfg.lookahead == (1 if cfg.rounds >= 8 else 0)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(E * cfg.rounds)]
     for e in evs:
         e.record()
-    binding.apsp_fw(t, events=evs)
+    binding.apsp_fw(t, events=evs, flags=flags)
     torch.cuda.synchronize()
-    assert all(evs[i].elapsed_time(evs[i + 1]) >= 0 for i in range(len(evs) - 1))
+
+    def le(i, j):
+        return evs[i].elapsed_time(evs[j]) >= 0
+
+    R = cfg.rounds
+    if not lookahead:  # one stream: every event in order
+        assert all(le(i, i + 1) for i in range(len(evs) - 1))
+    else:
+        for r in range(R):
+            assert le(E * r, E * r + 1) and le(E * r + 1, E * r + 2)   # phases 1, 2 of stage r
+            assert le(E * r + 2, E * r + 3) and le(E * r + 3, E * r + 4)  # phase 3 after phase 2
+            if r + 1 < R:
+                assert le(E * r + 2, E * (r + 1))      # stage r+1 starts after phase 2 of stage r
+                assert le(E * r + 4, E * (r + 1) + 3)  # phase-3 launches in stage order
     assert_fp32_close(t.cpu().numpy(), oracle.fw_f64(w))
