@@ -159,21 +159,32 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _measured_traffic(dtype: str, n: int, s: int):
-    """DRAM bytes per phase-3 launch from the committed ncu record, scaled by
-    the number of tiles; None if the kernels changed since it was taken."""
+KERNEL_SOURCES = ("fw_kernels.cuh", "tileset.h", "apsp_common.cuh")
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the device-code sources of the phase kernels."""
     import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1001_4108_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def _measured_traffic(dtype: str, n: int, s: int, tiles: float):
+    """DRAM bytes per phase-3 launch from the committed ncu record, scaled by
+    the number of tiles of the launch; None if the kernels changed since it
+    was taken."""
     rec_path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_1001_4108_gb300", "csrc", "fw_kernels.cuh")
     if not os.path.exists(rec_path):
         return None
     rec = json.load(open(rec_path))
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec.get("fw_kernels_sha256"):
+    if kernel_source_hash() != rec.get("kernel_sources_sha256"):
         return None
     e = rec.get(dtype)
     if not e or e["s"] != s or n <= s:
         return None
-    return e["bytes_per_launch"] * ((n - s) / s) ** 2 / ((e["n"] - s) / s) ** 2
+    return e["bytes_per_launch"] / e["tiles_per_launch"] * tiles
 
 
 def cpu_baseline(dtype: str, n_sample: int = 2048):
@@ -552,8 +563,9 @@ def run_ours(a):
                                    "per clock per SM (one 32-bit min per candidate on 64 ALU-pipe lanes; "
                                    "int16x2: 2 per DPX lane)",
                      "form_ceiling": form_ceiling, "frac_of_form_ceiling": achieved / form_ceiling,
-                     "traffic": _measured_traffic(a.dtype, n, cfg.kblock),
-                     "traffic_source": "ncu dram__bytes_read+write of the same kernel at n=8192, scaled by tile count",
+                     "traffic": _measured_traffic(a.dtype, n, S, p3_relax_mean / S ** 3),
+                     "traffic_source": "ncu dram__bytes_read+write of the same launch kind at n=8192, "
+                                       "scaled by tile count",
                      "algorithmic_hbm_GBps": hbm_bytes / p3_mean_s / 1e9,
                      "hbm_peak_GBps": peaks.get("hbm_gbs"),
                      "phase3_ms_mean": p3_mean_s * 1e3, "phase3_relax_per_launch": p3_relax_mean,

@@ -49,13 +49,18 @@ struct TileSet {
     return t;
   }
   // Tile of CTA t (0 <= t < total()); consecutive t share a tile row.
+  // Segments are picked with constant indices only, so that a kernel
+  // parameter of this type is read in place (no local-memory copy).
   APSP_HD void tile(int t, int &I, int &J) const {
-    int i = 0;
-    while (i + 1 < nseg && t >= count[i]) {
-      t -= count[i];
-      ++i;
+    TileSeg s = seg[0];
+    if (nseg > 1 && t >= count[0]) {
+      t -= count[0];
+      s = seg[1];
+      if (nseg > 2 && t >= count[1]) {
+        t -= count[1];
+        s = seg[2];
+      }
     }
-    const TileSeg &s = seg[i];
     if (s.row >= 0 && s.col >= 0) {
       I = s.row;
       J = s.col;
