@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--batched", type=int, default=4096, help="graphs in the batched (c4) comparison; 0 = skip")
     ap.add_argument("--serving", type=int, default=240, help="requests in the serving (c5) sweep; 0 = skip")
+    ap.add_argument("--paths", type=int, default=1, help="time the solve with path bookkeeping; 0 = skip")
     return ap.parse_args()
 
 
@@ -205,6 +206,52 @@ def cpu_baseline(dtype: str, n_sample: int = 2048):
             "sample": f"one Fig. 1 solve ({'FP64' if dtype == 'f32' else 'int64'}, single thread) of the same "
                       f"generator at n={n_sample} ({dt:.2f} s); relaxations/s scale as n^3 / t",
             "host_cpus": os.cpu_count()}
+
+
+def bench_paths(work, pristine, plain_ms: float, kblock: int, steps: int = 2, samples: int = 64):
+    """apsp_fw_paths on the bench workload (same device matrix) against the
+    plain solve's time; a few reconstructed paths are checked: each is a walk
+    along edges of the input whose weight (summed in FP64) is the solved
+    distance within the fp32 tolerance."""
+    import numpy as np
+    import torch
+    from paper_1001_4108_gb300 import binding
+    n = work.shape[0]
+    via = torch.empty((n, n), dtype=torch.int16, device="cuda")
+    work.copy_(pristine)
+    binding.apsp_fw_paths(work, via)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(steps):
+        work.copy_(pristine)
+        torch.cuda.synchronize()
+        e0.record()
+        binding.apsp_fw_paths(work, via)
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / steps
+    g = np.random.default_rng(0)
+    ii, jj = g.integers(0, n, samples), g.integers(0, n, samples)
+    dist = work.cpu().numpy()
+    vrec = via.cpu().numpy()
+    w = pristine.cpu().numpy()
+    ok, hops = True, []
+    for i, j in zip(ii.tolist(), jj.tolist()):
+        try:
+            p = binding.path(dist, vrec, i, j, kblock)
+        except binding.ApspError:
+            ok = False
+            continue
+        walk = sum(float(w[u, v]) for u, v in zip(p[:-1], p[1:]))
+        ok &= p[0] == i and p[-1] == j and abs(walk - float(dist[i, j])) <= 1e-5 * max(abs(float(dist[i, j])), 1.0)
+        hops.append(len(p) - 1)
+    del via
+    return {"ms_per_solve": ms, "plain_ms_per_solve": plain_ms, "overhead": ms / plain_ms,
+            "via_bytes": n * n * 2, "paths_checked": samples, "paths_valid": bool(ok),
+            "mean_edges_per_path": float(np.mean(hops)),
+            "timing": "CUDA events; matrix restore outside the timed region"}
 
 
 def bench_batched(count: int = 4096, steps: int = 3, seed: int = 5):
@@ -577,6 +624,8 @@ def run_ours(a):
         "paper_context": {"seconds_n16384_fp32_tesla_c1060": PAPER_SECONDS_N16384,
                           "ours_seconds": total_ms / a.steps / 1e3},
     }
+    if a.paths > 0:
+        line["paths"] = bench_paths(work, pristine, total_ms / a.steps, S)
     if a.batched > 0:
         line["batched"] = bench_batched(a.batched)
     if a.serving > 0:

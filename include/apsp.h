@@ -180,6 +180,36 @@ APSP_API int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const apsp
 APSP_API int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, void *stream);
 
 /*
+ * Shortest paths, not only their lengths (the paper computes distances only,
+ * Sec. 3.1; this is the path-reconstruction extension).
+ *
+ * apsp_fw_paths: apsp_fw_ex plus a stage record.  via (device, int16,
+ * row-major, leading dimension via_ld >= n elements, owned by the caller,
+ * written in full) receives, for every pair, the stage b (k-block b of
+ * Fig. 2) whose relaxations last strictly lowered d_ij, or -1 if d_ij kept its
+ * input value.  Every phase kernel compares the values it computes with the
+ * ones they replace; distances are bit-identical to apsp_fw_ex.  The stage
+ * numbers refer to the k-block depth of the solve (apsp_config.kblock for
+ * the same n, dtype and options.kblock).  APSP_EUNSUPPORTED if the number of
+ * stages exceeds 32767; other errors as apsp_fw_ex.
+ *
+ * apsp_path: one path i -> j from HOST copies of the solved matrix and of
+ * via (same layouts and dtype as the solve; kblock = that solve's k-block
+ * depth).  Writes the vertices i, ..., j to path (cap entries) and their
+ * number to *len: 1 for i == j, 0 if j is unreachable from i.  Block b of a
+ * pair (u, v) holds a vertex k with d_uk + d_kv = d_uv (integers: exactly,
+ * since the last improvement used values that no later stage lowered;
+ * fp32: the k whose rounded sum is nearest d_uv); the path is the edge
+ * u -> v for -1, else path(u, k) + path(k, v).  APSP_ENOMEM if cap is too
+ * small (*len then holds the length needed), APSP_EINVAL for bad arguments or
+ * a record that does not match the matrix.
+ */
+APSP_API int apsp_fw_paths(void *dist, int16_t *via, int64_t n, int64_t ld, int64_t via_ld, int dtype,
+                           const apsp_options *opt, void *stream);
+APSP_API int apsp_path(const void *dist, const int16_t *via, int64_t n, int64_t ld, int64_t via_ld, int dtype,
+                       int32_t kblock, int64_t i, int64_t j, int64_t *path, int64_t cap, int64_t *len);
+
+/*
  * Device workspace (bytes) a solve of this size uses; 0 if none.  fp32 solves
  * keep a k-pair-interleaved copy of the current pivot row panel there, int16
  * solves a copy of the current pivot column panel with every entry duplicated

@@ -29,7 +29,7 @@ EXPORTS = ["apsp_status_str", "apsp_version", "apsp_fw", "apsp_fw_ex", "apsp_fw_
            "apsp_workspace_bytes", "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus",
            "apsp_fw_f32_noalloc", "apsp_fw_batched", "apsp_autotune", "apsp_tuning_save",
            "apsp_tuning_load", "apsp_server_create", "apsp_submit", "apsp_poll", "apsp_wait",
-           "apsp_server_stats", "apsp_server_destroy"]
+           "apsp_server_stats", "apsp_server_destroy", "apsp_fw_paths", "apsp_path"]
 
 
 class Options(ctypes.Structure):
@@ -93,6 +93,9 @@ def lib() -> ctypes.CDLL:
             L.apsp_fw_ex.argtypes = [vp, i64, i64, i32, ctypes.POINTER(Options), vp]
             L.apsp_fw_host.argtypes = [vp, i64, i64, i32, vp]
             L.apsp_fw_f32_noalloc.argtypes = [vp, i64, i64, vp]
+            L.apsp_fw_paths.argtypes = [vp, vp, i64, i64, i64, i32, ctypes.POINTER(Options), vp]
+            L.apsp_path.argtypes = [vp, vp, i64, i64, i64, i32, ctypes.c_int32, i64, i64,
+                                    ctypes.POINTER(ctypes.c_int64), i64, ctypes.POINTER(ctypes.c_int64)]
             L.apsp_autotune.argtypes = [i32, vp, ctypes.c_char_p, i64]
             L.apsp_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)]
             L.apsp_submit.argtypes = [vp, vp, i64, i64, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
@@ -174,6 +177,41 @@ def apsp_fw(d, n: int | None = None, *, kblock: int = 0, flags: int = 0, events=
         opt.n_events = len(events)
     _check(lib().apsp_fw_ex(ptr, n, ld, dt, ctypes.byref(opt), s), "apsp_fw_ex")
     return d
+
+
+def apsp_fw_paths(d, via, n: int | None = None, *, kblock: int = 0, flags: int = 0, stream=None):
+    """apsp_fw plus the stage record: ``via`` is an int16 CUDA tensor (n x n or
+    wider) that receives, per pair, the stage of the last improvement (-1:
+    never improved).  Returns (d, via)."""
+    import torch
+    ptr, n, ld, dt = _matrix_args(d, n)
+    assert via.is_cuda and via.dtype == torch.int16 and via.dim() == 2 and via.stride(1) == 1
+    assert via.shape[0] >= n and via.shape[1] >= n
+    opt = Options(kblock, flags, None, 0, None, 0)
+    _check(lib().apsp_fw_paths(ptr, via.data_ptr(), n, ld, via.stride(0), dt, ctypes.byref(opt),
+                               _stream_handle(stream)), "apsp_fw_paths")
+    return d, via
+
+
+def path(dist, via, i: int, j: int, kblock: int) -> list:
+    """One shortest path i -> j (list of vertices; [] if unreachable) from
+    host (numpy) copies of a solved matrix and its stage record."""
+    import numpy as np
+    assert dist.ndim == 2 and via.ndim == 2 and via.dtype == np.int16
+    assert dist.strides[1] == dist.itemsize and via.strides[1] == 2
+    n = dist.shape[0]
+    cap = ctypes.c_int64(0)
+    ln = ctypes.c_int64(0)
+    args = (dist.ctypes.data, via.ctypes.data, n, dist.strides[0] // dist.itemsize, via.strides[0] // 2,
+            dtype_code(dist.dtype), kblock, i, j)
+    st = lib().apsp_path(*args, None, 0, ctypes.byref(ln))
+    if st == APSP_OK and ln.value == 0:
+        return []
+    if st != APSP_ENOMEM:
+        _check(st, "apsp_path")
+    buf = (ctypes.c_int64 * ln.value)()
+    _check(lib().apsp_path(*args, buf, ln.value, ctypes.byref(ln)), "apsp_path")
+    return list(buf[:ln.value])
 
 
 def apsp_fw_batched(mats, stream=None, ns=None):

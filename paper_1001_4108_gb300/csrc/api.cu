@@ -149,9 +149,11 @@ struct GraphKey {
   int dtype, S, flags, dev;
   cudaStream_t stream;
   void *ws;
+  void *via;
+  int64_t via_ld;
   bool operator==(const GraphKey &o) const {
     return d == o.d && n == o.n && ld == o.ld && dtype == o.dtype && S == o.S && flags == o.flags &&
-           dev == o.dev && stream == o.stream && ws == o.ws;
+           dev == o.dev && stream == o.stream && ws == o.ws && via == o.via && via_ld == o.via_ld;
   }
 };
 struct GraphEntry {
@@ -165,7 +167,7 @@ std::vector<GraphKey> g_seen;
 cudaStream_t g_capture_stream[kMaxDev];
 
 int launch_with_graph(const RunArgs &a, int dtype, int dev) {
-  const GraphKey key{a.d, a.n, a.ld, dtype, a.S, a.flags, dev, a.stream, a.ws};
+  const GraphKey key{a.d, a.n, a.ld, dtype, a.S, a.flags, dev, a.stream, a.ws, a.via, a.via_ld};
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto &g : g_graphs)
     if (g.key == key) return cudaGraphLaunch(g.exec, a.stream) == cudaSuccess ? APSP_OK : APSP_ECUDA;
@@ -349,7 +351,11 @@ extern "C" int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_conf
   return APSP_OK;
 }
 
-extern "C" int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt, void *stream) {
+namespace apsp {
+namespace {
+// apsp_fw_ex, optionally with the path bookkeeping of apsp_fw_paths.
+int solve(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt, void *stream, int16_t *via,
+          int64_t via_ld) {
   int st = check_args(dist, n, ld, dtype, opt);
   if (st != APSP_OK) return st;
   if (n == 0) return APSP_OK;
@@ -369,6 +375,8 @@ extern "C" int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const ap
   a.n_events = opt ? opt->n_events : 0;
   a.stream = static_cast<cudaStream_t>(stream);
   a.err = err;
+  a.via = via;
+  a.via_ld = via_ld;
   const size_t es = (size_t)elem_size(dtype);
   a.tma_ok = (reinterpret_cast<uintptr_t>(dist) % 16 == 0) && ((size_t)ld * es) % 16 == 0;
 
@@ -392,11 +400,30 @@ extern "C" int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const ap
     std::lock_guard<std::mutex> lk(g_mu);
     side_resources_locked(dev, a.stream, cap != cudaStreamCaptureStatusNone, &a);
   }
+  if (via && cudaMemset2DAsync(via, (size_t)via_ld * sizeof(int16_t), 0xff, (size_t)n * sizeof(int16_t), (size_t)n,
+                               a.stream) != cudaSuccess)  // every entry -1: never improved
+    return APSP_ECUDA;
   const bool direct = (a.flags & APSP_FLAG_NO_GRAPH) || a.events || cap != cudaStreamCaptureStatusNone;
   st = direct ? run_dtype(a, dtype) : launch_with_graph(a, dtype, dev);
   if (st != APSP_OK) return st;
   if (a.flags & APSP_FLAG_NEGCYCLE) return check_negcycle(dist, n, ld, dtype, a.stream, neg);
   return APSP_OK;
+}
+}  // namespace
+}  // namespace apsp
+
+extern "C" int apsp_fw_ex(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt, void *stream) {
+  return solve(dist, n, ld, dtype, opt, stream, nullptr, 0);
+}
+
+extern "C" int apsp_fw_paths(void *dist, int16_t *via, int64_t n, int64_t ld, int64_t via_ld, int dtype,
+                             const apsp_options *opt, void *stream) {
+  const int st = check_args(dist, n, ld, dtype, opt);
+  if (st != APSP_OK) return st;
+  if (n > 0 && (!via || via_ld < n)) return APSP_EINVAL;
+  const int S = choose_kblock(n, dtype, opt ? opt->kblock : 0);
+  if ((n + S - 1) / S > 32767) return APSP_EUNSUPPORTED;  // stage numbers must fit int16
+  return solve(dist, n, ld, dtype, opt, stream, via, via_ld);
 }
 
 extern "C" int apsp_fw(void *dist, int64_t n, int64_t ld, int dtype, void *stream) {

@@ -25,6 +25,10 @@ struct RunArgs {
   cudaStream_t side;
   cudaEvent_t fork, join;
   int side_prio;      // launch priority of the side-stream kernels
+  // Optional path bookkeeping: via[i * via_ld + j] = stage of the last strict
+  // improvement of d_ij (nullptr = off).
+  int16_t *via;
+  int64_t via_ld;
 };
 
 // Events a traced solve records per stage (apsp_options.events).

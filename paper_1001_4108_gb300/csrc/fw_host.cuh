@@ -21,7 +21,7 @@ template <> struct TmaType<float> { static constexpr CUtensorMapDataType v = CU_
 // column panel in the workspace (S words x n_p rows, 128-byte swizzle).
 template <int S>
 static bool make_s16_maps(int16_t *d, int64_t n, int64_t ld, uint32_t *arep, int64_t np, CUtensorMap *mA16,
-                          CUtensorMap *mB16, CUtensorMap *mArep) {
+                          CUtensorMap *mB16, CUtensorMap *mArep, CUtensorMap *mC16) {
   EncodeTiledFn enc = encode_tiled_fn();
   if (!enc) return false;
   const cuuint32_t estr[2] = {1, 1};
@@ -34,6 +34,11 @@ static bool make_s16_maps(int16_t *d, int64_t n, int64_t ld, uint32_t *arep, int
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
   if (enc(mB16, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, d, dims, strides, boxB, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const cuuint32_t boxC[2] = {(cuuint32_t)S, (cuuint32_t)S};  // the whole C tile (deferred form)
+  if (enc(mC16, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, d, dims, strides, boxC, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
@@ -139,7 +144,7 @@ static cudaError_t launch(void (*k)(KP...), dim3 grid, int threads, size_t smem,
 // CTAs retire: the mostly serial phase 1 and the one-wave phase 2 no longer
 // leave the GPU idle between the phase-3 launches.  Every tile still sees
 // every stage in order, so results equal the plain schedule's bit for bit.
-template <typename T, int S, bool HAS_TMA>
+template <typename T, int S, bool HAS_TMA, bool VIA>
 static int run_rounds(const RunArgs &a) {
   using K = Kernels<T, S>;
   static thread_local int setup_done_mask = 0;  // bit per device
@@ -148,25 +153,25 @@ static int run_rounds(const RunArgs &a) {
   if (!(setup_done_mask & (1 << (dev & 31)))) {
     if (K::setup() != cudaSuccess) return APSP_ECUDA;
     if constexpr (HAS_TMA) {
-      if (cudaFuncSetAttribute(fw_tile_tma<T, S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if (cudaFuncSetAttribute(fw_tile_tma<T, S, 0, VIA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                P3Tma<S>::SMEM) != cudaSuccess ||
-          cudaFuncSetAttribute(fw_tile_tma<T, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          cudaFuncSetAttribute(fw_tile_tma<T, S, 1, VIA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                P3Tma<S>::SMEM) != cudaSuccess)
         return APSP_ECUDA;
       if constexpr (std::is_same<T, float>::value) {
         const int sm = P3Tma<S>::SMEM;
         const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        if (cudaFuncSetAttribute(fw_phase3_f32x2<S, false, true>, attr, sm) != cudaSuccess ||
-            cudaFuncSetAttribute(fw_phase3_f32x2<S, true, true>, attr, sm) != cudaSuccess ||
-            cudaFuncSetAttribute(fw_phase3_f32x2<S, false, false>, attr, sm) != cudaSuccess ||
-            cudaFuncSetAttribute(fw_phase3_f32x2<S, true, false>, attr, sm) != cudaSuccess)
+        if (cudaFuncSetAttribute(fw_phase3_f32x2<S, false, true, VIA>, attr, sm) != cudaSuccess ||
+            cudaFuncSetAttribute(fw_phase3_f32x2<S, true, true, VIA>, attr, sm) != cudaSuccess ||
+            cudaFuncSetAttribute(fw_phase3_f32x2<S, false, false, VIA>, attr, sm) != cudaSuccess ||
+            cudaFuncSetAttribute(fw_phase3_f32x2<S, true, false, VIA>, attr, sm) != cudaSuccess)
           return APSP_ECUDA;
       }
     }
     if constexpr (std::is_same<T, int16_t>::value) {
       const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-      if (cudaFuncSetAttribute(fw_tile_s16x2<S, 0>, attr, P3S16<S>::SMEM) != cudaSuccess ||
-          cudaFuncSetAttribute(fw_tile_s16x2<S, 1>, attr, P3S16<S>::SMEM) != cudaSuccess)
+      if (cudaFuncSetAttribute(fw_tile_s16x2<S, 0, VIA>, attr, P3S16<S>::SMEM_P3) != cudaSuccess ||
+          cudaFuncSetAttribute(fw_tile_s16x2<S, 1, VIA>, attr, P3S16<S>::SMEM) != cudaSuccess)
         return APSP_ECUDA;
     }
     setup_done_mask |= 1 << (dev & 31);
@@ -203,7 +208,7 @@ static int run_rounds(const RunArgs &a) {
     }
   }
 
-  CUtensorMap mA16, mB16, mArep[2];
+  CUtensorMap mA16, mB16, mC16, mArep[2];
   bool use_s16 = false;
   uint32_t *arep[2] = {nullptr, nullptr};
   if constexpr (std::is_same<T, int16_t>::value) {
@@ -215,7 +220,7 @@ static int run_rounds(const RunArgs &a) {
       for (int i = 0; i < nbuf; ++i) {
         arep[i] = reinterpret_cast<uint32_t *>(static_cast<char *>(a.ws) + i * pb);
         use_s16 = use_s16 && make_s16_maps<S>(reinterpret_cast<int16_t *>(d), n, ld, arep[i], np, &mA16, &mB16,
-                                              &mArep[i]);
+                                              &mArep[i], &mC16);
       }
       if (!use_s16) nbuf = 0;
     }
@@ -239,8 +244,9 @@ static int run_rounds(const RunArgs &a) {
   // ---- the three phases of one stage, on stream s with priority prio
   auto phase1 = [&](int b, cudaStream_t s, int prio) -> cudaError_t {
     const int last = b == R - 1 ? 1 : 0;
-    if (prio != 0) return launch(fw_phase1_side<T, S>, dim3(1), K::NT1_SIDE, 0, s, prio, d, n, ld, b, last);
-    return launch(fw_phase1<T, S>, dim3(1), K::NT1, 0, s, 0, d, n, ld, b, last);
+    if (prio != 0)
+      return launch(fw_phase1_side<T, S>, dim3(1), K::NT1_SIDE, 0, s, prio, d, n, ld, b, last, a.via, a.via_ld);
+    return launch(fw_phase1<T, S>, dim3(1), K::NT1, 0, s, 0, d, n, ld, b, last, a.via, a.via_ld);
   };
   auto phase2 = [&](int b, cudaStream_t s, int prio) -> cudaError_t {
     if (R == 1) return cudaSuccess;
@@ -248,16 +254,18 @@ static int run_rounds(const RunArgs &a) {
     const dim3 g(2 * (R - 1));
     if constexpr (std::is_same<T, int16_t>::value) {
       if (use_s16 && full_k(b))
-        return launch(fw_tile_s16x2<S, 1>, g, P3S16<S>::TPB, P3S16<S>::SMEM, s, prio, mA16, mB16,
-                      reinterpret_cast<int16_t *>(d), n, ld, b, R, TileSet{}, reverse, arep[buf_of(b)], a.err);
+        return launch(fw_tile_s16x2<S, 1, VIA>, g, P3S16<S>::TPB, P3S16<S>::SMEM, s, prio, mA16, mB16, mC16,
+                      reinterpret_cast<int16_t *>(d), n, ld, b, R, TileSet{}, reverse, arep[buf_of(b)], a.via,
+                      a.via_ld, a.err);
     }
     T *bpb = (use_packed && full_k(b)) ? bp[buf_of(b)] : nullptr;
     if constexpr (HAS_TMA) {
       if (use_tma && full_k(b))
-        return launch(fw_tile_tma<T, S, 1>, g, P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB, d, n, ld, b, R,
-                      TileSet{}, last, reverse, bpb, 2 * np, a.err);
+        return launch(fw_tile_tma<T, S, 1, VIA>, g, P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB, d, n, ld, b, R,
+                      TileSet{}, last, reverse, bpb, 2 * np, a.via, a.via_ld, a.err);
     }
-    return launch(fw_phase2<T, S, K::NT2>, g, K::NT2, K::SM2, s, prio, d, n, ld, b, R, last, bpb, 2 * np);
+    return launch(fw_phase2<T, S, K::NT2>, g, K::NT2, K::SM2, s, prio, d, n, ld, b, R, last, bpb, 2 * np, a.via,
+                  a.via_ld);
   };
   // phase 3 of stage b over the tiles of `kind`
   auto phase3 = [&](int b, int kind, cudaStream_t s, int prio) -> cudaError_t {
@@ -268,9 +276,9 @@ static int run_rounds(const RunArgs &a) {
         if (use_s16) {
           const TileSet ts = make_tileset(kind, kPartAny, b, R, ragged);
           if (ts.total() == 0) return cudaSuccess;
-          return launch(fw_tile_s16x2<S, 0>, dim3(ts.total()), P3S16<S>::TPB, P3S16<S>::SMEM, s, prio,
-                        mArep[buf_of(b)], mB16, reinterpret_cast<int16_t *>(d), n, ld, b, R, ts, reverse,
-                        arep[buf_of(b)], a.err);
+          return launch(fw_tile_s16x2<S, 0, VIA>, dim3(ts.total()), P3S16<S>::TPB, P3S16<S>::SMEM_P3, s, prio,
+                        mArep[buf_of(b)], mB16, mC16, reinterpret_cast<int16_t *>(d), n, ld, b, R, ts, reverse,
+                        arep[buf_of(b)], a.via, a.via_ld, a.err);
         }
       }
       if constexpr (std::is_same<T, float>::value) {
@@ -281,15 +289,15 @@ static int run_rounds(const RunArgs &a) {
           const TileSet te = make_tileset(kind, kPartEdge, b, R, ragged);
           cudaError_t e = cudaSuccess;
           if (ti.total() > 0)
-            e = reverse ? launch(fw_phase3_f32x2<S, true, true>, dim3(ti.total()), tpb, sm, s, prio, mA, mb, d,
-                                 n, ld, b, ti, a.err)
-                        : launch(fw_phase3_f32x2<S, false, true>, dim3(ti.total()), tpb, sm, s, prio, mA, mb, d,
-                                 n, ld, b, ti, a.err);
+            e = reverse ? launch(fw_phase3_f32x2<S, true, true, VIA>, dim3(ti.total()), tpb, sm, s, prio, mA, mb, d,
+                                 n, ld, b, ti, a.via, a.via_ld, a.err)
+                        : launch(fw_phase3_f32x2<S, false, true, VIA>, dim3(ti.total()), tpb, sm, s, prio, mA, mb, d,
+                                 n, ld, b, ti, a.via, a.via_ld, a.err);
           if (e == cudaSuccess && te.total() > 0)
-            e = reverse ? launch(fw_phase3_f32x2<S, true, false>, dim3(te.total()), tpb, sm, s, prio, mA, mb, d,
-                                 n, ld, b, te, a.err)
-                        : launch(fw_phase3_f32x2<S, false, false>, dim3(te.total()), tpb, sm, s, prio, mA, mb, d,
-                                 n, ld, b, te, a.err);
+            e = reverse ? launch(fw_phase3_f32x2<S, true, false, VIA>, dim3(te.total()), tpb, sm, s, prio, mA, mb, d,
+                                 n, ld, b, te, a.via, a.via_ld, a.err)
+                        : launch(fw_phase3_f32x2<S, false, false, VIA>, dim3(te.total()), tpb, sm, s, prio, mA, mb, d,
+                                 n, ld, b, te, a.via, a.via_ld, a.err);
           return e;
         }
       }
@@ -297,14 +305,14 @@ static int run_rounds(const RunArgs &a) {
         if (use_tma) {
           const TileSet ts = make_tileset(kind, kPartAny, b, R, ragged);
           if (ts.total() == 0) return cudaSuccess;
-          return launch(fw_tile_tma<T, S, 0>, dim3(ts.total()), P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB, d,
-                        n, ld, b, R, ts, last, reverse, (T *)nullptr, (int64_t)0, a.err);
+          return launch(fw_tile_tma<T, S, 0, VIA>, dim3(ts.total()), P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB, d,
+                        n, ld, b, R, ts, last, reverse, (T *)nullptr, (int64_t)0, a.via, a.via_ld, a.err);
         }
       }
     }
     // generic kernel: all tiles of the stage (plain schedule only)
     return launch(fw_phase3_generic<T, S>, dim3(R - 1, R - 1), 256, K::SM3G, s, prio, d, n, ld, b, last,
-                  reverse);
+                  reverse, a.via, a.via_ld);
   };
 
   const int E = kEventsPerStage;
@@ -340,8 +348,8 @@ template <typename T, bool HAS_TMA>
 static int run_any(const RunArgs &a) {
   if (a.n == 0) return APSP_OK;
   switch (a.S) {
-    case 64: return run_rounds<T, 64, HAS_TMA>(a);
-    case 128: return run_rounds<T, 128, HAS_TMA>(a);
+    case 64: return a.via ? run_rounds<T, 64, HAS_TMA, true>(a) : run_rounds<T, 64, HAS_TMA, false>(a);
+    case 128: return a.via ? run_rounds<T, 128, HAS_TMA, true>(a) : run_rounds<T, 128, HAS_TMA, false>(a);
     default: return APSP_EINVAL;
   }
 }

@@ -24,6 +24,16 @@
 
 namespace apsp {
 
+// Path bookkeeping (optional, via != nullptr): via[i][j] = the stage b whose
+// k-block last strictly improved d_ij.  Each store site compares the new
+// value with the one it replaces; stages run in order, so the last stage to
+// write is the last improvement.  The TMA-staged kernels compile it only in
+// their VIA instances, so that the distance-only kernels keep their code.
+template <typename C>
+__device__ __forceinline__ void note_via(int16_t *via, int64_t via_ld, int64_t i, int64_t j, C now, C before, int b) {
+  if (now < before) via[i * via_ld + j] = (int16_t)b;
+}
+
 // ------------------------------------------------------------------ phase 1
 // One CTA closes the diagonal tile (b, b): s sequential k steps, each a rank-1
 // update x_ij <- min(x_ij, x_ik + x_kj) of the whole tile.
@@ -33,7 +43,8 @@ namespace apsp {
 // row/column k+1 publish them right after their own step-k update, into the
 // other half of a double buffer: one barrier per step.
 template <typename T, int S, int MR, int MC>
-__device__ __forceinline__ void phase1_body(T *__restrict__ d, int64_t n, int64_t ld, int b, int last) {
+__device__ __forceinline__ void phase1_body(T *__restrict__ d, int64_t n, int64_t ld, int b, int last,
+                                            int16_t *__restrict__ via, int64_t via_ld) {
   using C = typename Arith<T>::C;
   constexpr int QC = S / MC;  // thread columns
   constexpr int U = MR > MC ? MR : MC;  // k steps per unrolled group (MR, MC in {4, 8})
@@ -91,15 +102,18 @@ __device__ __forceinline__ void phase1_body(T *__restrict__ d, int64_t n, int64_
 #pragma unroll
     for (int c = 0; c < MC; ++c) {
       const int64_t gi = base + MR * ty + a, gj = base + MC * tx + c;
-      if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(x[a][c]) : (T)x[a][c];
+      if (gi < n && gj < n) {
+        if (via) note_via(via, via_ld, gi, gj, x[a][c], Arith<T>::load(d[gi * ld + gj]), b);
+        d[gi * ld + gj] = last ? Arith<T>::finish(x[a][c]) : (T)x[a][c];
+      }
     }
 }
 
 // Alone on the GPU: 4 x 4 blocks, the most threads (latency bound).
 template <typename T, int S>
 __global__ void __launch_bounds__((S / 4) * (S / 4)) fw_phase1(T *__restrict__ d, int64_t n, int64_t ld, int b,
-                                                               int last) {
-  phase1_body<T, S, 4, 4>(d, n, ld, b, last);
+                                                               int last, int16_t *via, int64_t via_ld) {
+  phase1_body<T, S, 4, 4>(d, n, ld, b, last, via, via_ld);
 }
 
 // Beside phase 3 (lookahead schedule): 8 x 4 blocks and at most 64 registers
@@ -107,8 +121,8 @@ __global__ void __launch_bounds__((S / 4) * (S / 4)) fw_phase1(T *__restrict__ d
 // (S = 128: 512 threads x 64 registers = 32768).
 template <typename T, int S>
 __global__ void __launch_bounds__((S / 8) * (S / 4), S == 128 ? 2 : 4)
-    fw_phase1_side(T *__restrict__ d, int64_t n, int64_t ld, int b, int last) {
-  phase1_body<T, S, 8, 4>(d, n, ld, b, last);
+    fw_phase1_side(T *__restrict__ d, int64_t n, int64_t ld, int b, int last, int16_t *via, int64_t via_ld) {
+  phase1_body<T, S, 8, 4>(d, n, ld, b, last, via, via_ld);
 }
 
 // ------------------------------------------------------------------ phase 2
@@ -124,7 +138,8 @@ __global__ void __launch_bounds__((S / 8) * (S / 4), S == 128 ? 2 : 4)
 // the layout the packed fp32 phase-3 kernel reads.
 template <typename T, int S, int NT>
 __global__ void __launch_bounds__(NT) fw_phase2(T *__restrict__ d, int64_t n, int64_t ld, int b, int R, int last,
-                                                T *__restrict__ bp, int64_t bp_ld) {
+                                                T *__restrict__ bp, int64_t bp_ld, int16_t *__restrict__ via,
+                                                int64_t via_ld) {
   using C = typename Arith<T>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *D = reinterpret_cast<C *>(smem_raw);
@@ -174,6 +189,7 @@ __global__ void __launch_bounds__(NT) fw_phase2(T *__restrict__ d, int64_t n, in
     const int i = i0 + RS * r;
     if (r0 + i < n && c0 + j < n) {
       const C v = X[i * S + j];
+      if (via) note_via(via, via_ld, r0 + i, c0 + j, v, Arith<T>::load(d[(r0 + i) * ld + c0 + j]), b);
       d[(r0 + i) * ld + c0 + j] = last ? Arith<T>::finish(v) : (T)v;
     }
   }
@@ -193,7 +209,8 @@ __global__ void __launch_bounds__(NT) fw_phase2(T *__restrict__ d, int64_t n, in
 // matrix.  grid = (R-1, R-1).
 template <typename T, int S>
 __global__ void __launch_bounds__(256) fw_phase3_generic(T *__restrict__ d, int64_t n, int64_t ld, int b,
-                                                         int last, int reverse) {
+                                                         int last, int reverse, int16_t *__restrict__ via,
+                                                         int64_t via_ld) {
   using C = typename Arith<T>::C;
   constexpr int M = S / 16;
   constexpr int AS = S + 1;  // padded row stride of the column panel
@@ -236,7 +253,10 @@ __global__ void __launch_bounds__(256) fw_phase3_generic(T *__restrict__ d, int6
 #pragma unroll
     for (int c = 0; c < M; ++c) {
       const int64_t gi = I0 + ty + 16 * r, gj = J0 + tx + 16 * c;
-      if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(acc[r][c]) : (T)acc[r][c];
+      if (gi < n && gj < n) {
+        if (via) note_via(via, via_ld, gi, gj, acc[r][c], Arith<T>::load(d[gi * ld + gj]), b);
+        d[gi * ld + gj] = last ? Arith<T>::finish(acc[r][c]) : (T)acc[r][c];
+      }
     }
 }
 
@@ -330,11 +350,11 @@ __device__ __forceinline__ void lds4(const T *p, T &x0, T &x1, T &x2, T &x3) {
   x3 = *reinterpret_cast<T *>(&e);
 }
 
-template <typename T, int S, int MODE>
+template <typename T, int S, int MODE, bool VIA = false>
 __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     fw_tile_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 T *__restrict__ d, int64_t n, int64_t ld, int b, int R, const TileSet ts, int last, int reverse,
-                T *__restrict__ bp, int64_t bp_ld, int *err) {
+                T *__restrict__ bp, int64_t bp_ld, int16_t *__restrict__ via, int64_t via_ld, int *err) {
   using P = P3Tma<S>;
   constexpr int G = P::G;
   constexpr int KS = P::KS;
@@ -474,6 +494,15 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
   I0 = (int64_t)It * S;
   J0 = (int64_t)Jt * S;
   const bool row_panel = MODE == 1 && It == b;
+  if (VIA && via) {  // path bookkeeping: compare with the values about to be replaced
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int64_t gi = I0 + ty + G * r, gj = J0 + (c / 4) * (S / 2) + 4 * tx + (c % 4);
+        if (gi < n && gj < n) note_via(via, via_ld, gi, gj, acc[r][c], d[gi * ld + gj], b);
+      }
+  }
   if (I0 + S <= n && J0 + S <= n) {
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -532,10 +561,11 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 // (a.x + b.x, a.y + b.y), each rounded to nearest: one packed add.f32x2.
 __device__ __forceinline__ float2 add2f(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
-template <int S, bool REVERSE, bool FULL>
+template <int S, bool REVERSE, bool FULL, bool VIA = false>
 __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     fw_phase3_f32x2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBp,
-                    float *__restrict__ d, int64_t n, int64_t ld, int b, const TileSet ts, int *err) {
+                    float *__restrict__ d, int64_t n, int64_t ld, int b, const TileSet ts,
+                    int16_t *__restrict__ via, int64_t via_ld, int *err) {
   using P = P3Tma<S>;
   constexpr int G = P::G;
   constexpr int KS = P::KS;
@@ -652,6 +682,17 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     rows_left = (int)(n - ((int64_t)It2 * S + ty2));
     cols_left = (int)(n - ((int64_t)Jt2 * S + 2 * tx2));
   }
+  if (VIA && via) {  // path bookkeeping: compare with the values about to be replaced
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int64_t gi = (int64_t)It2 * S + ty2 + G * r, gj = (int64_t)Jt2 * S + 2 * tx2 + 2 * G * m + e;
+          if (gi < n && gj < n) note_via(via, via_ld, gi, gj, acc[r][2 * m + e], d[gi * ld + gj], b);
+        }
+  }
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -692,29 +733,45 @@ template <int S> struct P3S16 {
   static constexpr int A_BYTES_REP = S * KS * 4;  // MODE 0
   static constexpr int A_BYTES_16 = S * KS * 2;   // MODE 1
   static constexpr int B_BYTES = KS * S * 2;
+  // Phase 3 at s = 128 also stages the C tile in shared memory (below).
+  static constexpr bool C_SMEM = S == 128;
+  static constexpr int C_BYTES = C_SMEM ? S * S * 2 : 0;
   static constexpr int SMEM = STAGES * (A_BYTES_REP + B_BYTES) + 1024 + 64;
+  static constexpr int SMEM_P3 = SMEM + C_BYTES;
 };
 
 __device__ __forceinline__ uint32_t rep_lo(uint32_t w) { return __byte_perm(w, 0, 0x1010); }
 __device__ __forceinline__ uint32_t rep_hi(uint32_t w) { return __byte_perm(w, 0, 0x3232); }
 
-template <int S, int MODE>
+//
+// Deferred C (phase 3, s = 128): the accumulators start at "infinity" and the
+// k-block runs right away; the C tile travels by TMA into shared memory
+// meanwhile and is folded in at the end, c <- min(c, min_k a_ik + b_kj).  The
+// minimum is exact and every value is <= 16383, so this equals starting from
+// c.  In the plain form every CTA of a wave first waits for its C tile, and
+// the CTAs of a wave, all equally long, issue those loads together.
+template <int S, int MODE, bool VIA = false>
 __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
     fw_tile_s16x2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  int16_t *__restrict__ d, int64_t n, int64_t ld, int b, int R, const TileSet ts, int reverse,
-                  uint32_t *__restrict__ arep, int *err) {
+                  const __grid_constant__ CUtensorMap tmC, int16_t *__restrict__ d, int64_t n, int64_t ld, int b,
+                  int R, const TileSet ts, int reverse, uint32_t *__restrict__ arep, int16_t *__restrict__ via,
+                  int64_t via_ld, int *err) {
   using P = P3S16<S>;
   constexpr int G = P::G;
   constexpr int KS = P::KS;
   constexpr int A_BYTES = MODE == 0 ? P::A_BYTES_REP : P::A_BYTES_16;
+  constexpr bool DEFER_C = MODE == 0 && P::C_SMEM;
+  constexpr int C_BYTES = DEFER_C ? P::C_BYTES : 0;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char *As = base;
   unsigned char *Bs = base + P::STAGES * A_BYTES;
-  uint64_t *full = reinterpret_cast<uint64_t *>(base + P::STAGES * (A_BYTES + P::B_BYTES));
+  unsigned char *Cs = Bs + P::STAGES * P::B_BYTES;  // C tile, S rows x S int16 (deferred form)
+  uint64_t *full = reinterpret_cast<uint64_t *>(Cs + C_BYTES);
+  uint64_t *cbar = full + P::STAGES;
 
-  int *tile_ij = reinterpret_cast<int *>(full + P::STAGES);  // (It, Jt), reread after the main loop
+  int *tile_ij = reinterpret_cast<int *>(cbar + 1);  // (It, Jt), reread after the main loop
 
   const int tid = threadIdx.x;
   const int tx = tid % G, ty = tid / G;
@@ -734,11 +791,16 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
     prefetch_tensormap(&tmB);
 #pragma unroll
     for (int s = 0; s < P::STAGES; ++s) mbar_init(&full[s], 1);
+    if (DEFER_C) mbar_init(cbar, 1);
     fence_mbar_init();
     tile_ij[0] = It;
     tile_ij[1] = Jt;
   }
   __syncthreads();
+  if (DEFER_C && tid == 0) {
+    mbar_arrive_expect_tx(cbar, P::C_BYTES);
+    tma_load_2d(Cs, &tmC, cbar, Jt * S, It * S);
+  }
   auto issue = [&](int s, int st) {
     const int i0 = lds_volatile(tile_ij) * S, j0 = lds_volatile(tile_ij + 1) * S;
     mbar_arrive_expect_tx(&full[st], A_BYTES + P::B_BYTES);
@@ -753,14 +815,17 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
     for (int s = 0; s < P::STAGES && s < P::NSL; ++s) issue(s, s);
   }
 
-  // C tile -> registers: 8 rows x 4 column pairs.
+  // C tile -> registers: 8 rows x 4 column pairs (deferred form: infinity).
   const bool full_tile = I0 + S <= n && J0 + S <= n;
   uint32_t acc[8][4];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int64_t gi = I0 + ty + G * r;
     const int64_t gj = J0 + 8 * tx;
-    if (full_tile) {
+    if (DEFER_C) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[r][m] = 16383u | (16383u << 16);
+    } else if (full_tile) {
       const uint4 v = *reinterpret_cast<const uint4 *>(d + gi * ld + gj);
       acc[r][0] = v.x; acc[r][1] = v.y; acc[r][2] = v.z; acc[r][3] = v.w;
     } else {
@@ -817,6 +882,31 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
     if (tid == 0 && s + P::STAGES < P::NSL) issue(s + P::STAGES, st);
   }
 
+  if (DEFER_C) {
+    // fold in the C tile (rows ty + G r, int16 columns 8 tx .. 8 tx + 7)
+    if (__syncthreads_or(!mbar_wait_bounded(cbar, 0))) {
+      if (tid == 0) atomicCAS(err, 0, (int)kDevTimeoutTma);
+      return;
+    }
+    const int64_t vi0 = (int64_t)lds_volatile(tile_ij) * S, vj0 = (int64_t)lds_volatile(tile_ij + 1) * S;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint4 c = *reinterpret_cast<const uint4 *>(Cs + (ty + G * r) * (S * 2) + 16 * tx);
+      const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (VIA && via) {  // path bookkeeping: the k-block result against the tile's value
+          const int64_t gi = vi0 + ty + G * r, gj = vj0 + 8 * tx + 2 * m;
+          if (gi < n && gj < n) note_via(via, via_ld, gi, gj, (int)(int16_t)(acc[r][m] & 0xffffu),
+                                          (int)(int16_t)(cw[m] & 0xffffu), b);
+          if (gi < n && gj + 1 < n) note_via(via, via_ld, gi, gj + 1, (int)(int16_t)(acc[r][m] >> 16),
+                                              (int)(int16_t)(cw[m] >> 16), b);
+        }
+        acc[r][m] = __vmins2(acc[r][m], cw[m]);
+      }
+    }
+  }
+
   // tile coordinates from shared memory: nothing of them stays live in
   // registers across the main loop
   It = lds_volatile(tile_ij);
@@ -825,6 +915,19 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
   J0 = (int64_t)Jt * S;
   const bool full_tile_out = I0 + S <= n && J0 + S <= n;
   const bool col_panel = MODE == 1 && It != b;
+  if (!DEFER_C && VIA && via) {  // path bookkeeping: compare with the values about to be replaced
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int64_t gi = I0 + ty + G * r, gj = J0 + 8 * tx + 2 * m + e;
+          if (gi < n && gj < n)
+            note_via(via, via_ld, gi, gj, (int)(int16_t)(e ? acc[r][m] >> 16 : acc[r][m] & 0xffffu),
+                     (int)d[gi * ld + gj], b);
+        }
+  }
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int64_t gi = I0 + ty + G * r;
