@@ -482,12 +482,18 @@ extern "C" int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, v
     hs.bytes = bytes;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpy2DAsync(hs.buf, dld * es, host_dist, ld * es, n * es, n, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return APSP_ECUDA;
+  // one linear copy each way when the rows are contiguous on both sides (a
+  // pitched copy of n rows moves the same bytes at a fraction of the rate)
+  const bool linear = ld == dld;
+  const size_t row = (size_t)n * es, hpitch = (size_t)ld * es, dpitch = (size_t)dld * es;
+  cudaError_t e = linear ? cudaMemcpyAsync(hs.buf, host_dist, bytes, cudaMemcpyHostToDevice, s)
+                         : cudaMemcpy2DAsync(hs.buf, dpitch, host_dist, hpitch, row, n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return APSP_ECUDA;
   st = apsp_fw_ex(hs.buf, n, dld, dtype, nullptr, stream);
   if (st != APSP_OK) return st;
-  if (cudaMemcpy2DAsync(host_dist, ld * es, hs.buf, dld * es, n * es, n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return APSP_ECUDA;
+  e = linear ? cudaMemcpyAsync(host_dist, hs.buf, bytes, cudaMemcpyDeviceToHost, s)
+             : cudaMemcpy2DAsync(host_dist, hpitch, hs.buf, dpitch, row, n, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return APSP_ECUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? APSP_OK : APSP_ECUDA;
 }
 
