@@ -346,6 +346,7 @@ def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), 
         m = len(arrivals)
         with server_factory() as srv:
             tickets = [None] * m
+            submitted = [threading.Event() for _ in range(m)]
             done = [None] * m
             outs = [None] * m
             errors = []
@@ -358,17 +359,20 @@ def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), 
                         if dt > 0:
                             time.sleep(dt)
                         tickets[i] = srv.submit(mats[i])
+                        submitted[i].set()
                 except BaseException as e:  # surfaced by the waiters below
                     errors.append(e)
+                finally:
+                    for ev in submitted:  # wake every waiter; they check the ticket
+                        ev.set()
 
             def waiter(i):
-                while tickets[i] is None:
-                    if errors:
-                        raise errors[0]
-                    if not th.is_alive() and tickets[i] is None:
-                        raise RuntimeError("submitter stopped early")
+                # blocks (no polling) until request i is submitted, then in
+                # apsp_wait until it is done
+                while not submitted[i].wait(0.5):
                     check_time()
-                    time.sleep(0.0002)
+                if tickets[i] is None:
+                    raise errors[0] if errors else RuntimeError("submitter stopped early")
                 out = srv.wait(tickets[i], timeout_s=max(1.0, time_limit_s - (time.perf_counter() - t_start)))
                 if out is None:
                     raise TimeoutError("request did not finish")

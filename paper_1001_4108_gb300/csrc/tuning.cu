@@ -75,6 +75,28 @@ int tuned_kblock(int64_t n, int dtype) { return n >= g_tab.kblock_cross[dtype_in
 
 using namespace apsp;
 
+namespace {
+// Runs fn() (enqueueing work on st, returning an apsp_status) between two
+// events on st and reports the elapsed milliseconds.
+template <typename F>
+int time_on_stream(cudaStream_t st, float *ms, F fn) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return APSP_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return APSP_ECUDA;
+  }
+  int rc = cudaEventRecord(e0, st) == cudaSuccess ? APSP_OK : APSP_ECUDA;
+  if (rc == APSP_OK) rc = fn();
+  if (rc == APSP_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess))
+    rc = APSP_ECUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+}  // namespace
+
 extern "C" int apsp_autotune(int dtype, void *stream, char *report, int64_t report_len) {
   if (dtype != APSP_I32 && dtype != APSP_F32 && dtype != APSP_I16) return APSP_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -131,13 +153,15 @@ extern "C" int apsp_autotune(int dtype, void *stream, char *report, int64_t repo
   }
   // ---- whole-batch assignment: the groups of a batch run concurrently and
   // compete for the SMs, so the per-bucket winners are checked against a few
-  // fixed assignments on a mixed batch (n uniform in 16..512, largest first)
+  // fixed assignments on a mixed batch (n uniform in 16..512, largest first).
+  // Each candidate: best of 3 timed runs; the default assignment (first) is
+  // kept unless another beats it by more than 1 %.
   rep += "], \"mixed\": [";
   {
-    const int cand[][kBuckets] = {{best_v[0], best_v[1], best_v[2], best_v[3], best_v[4]},
-                                  {1, 2, 2, 2, 2}, {1, 2, 2, 2, 3}, {0, 2, 2, 2, 2}, {2, 2, 2, 2, 2}, {1, 1, 2, 2, 2}};
+    const int cand[][kBuckets] = {{1, 2, 2, 2, 2}, {best_v[0], best_v[1], best_v[2], best_v[3], best_v[4]},
+                                  {1, 2, 2, 2, 3}, {0, 2, 2, 2, 2}, {2, 2, 2, 2, 2}, {1, 1, 2, 2, 2}};
     const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
-    const int count = 1024;
+    const int count = 2048;
     std::vector<BatchDesc> descs(count);
     size_t total = 0;
     for (int g = 0; g < count; ++g) {
@@ -167,20 +191,16 @@ extern "C" int apsp_autotune(int dtype, void *stream, char *report, int64_t repo
         for (int bk = 0; bk < kBuckets; ++bk) g_tab.batch_variant[di][bk] = cand[c][bk];
       }
       float ms = 0;
-      cudaEvent_t e0, e1;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
       rc = fill(mats, total, dtype, st);
       if (rc == APSP_OK) rc = run_batched_direct(descs.data(), count, dtype, st, &dbuf, &dcap);  // warm-up
-      if (rc == APSP_OK) rc = fill(mats, total, dtype, st);
-      cudaEventRecord(e0, st);
-      if (rc == APSP_OK) rc = run_batched_direct(descs.data(), count, dtype, st, &dbuf, &dcap);
-      cudaEventRecord(e1, st);
-      if (rc == APSP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-        rc = APSP_ECUDA;
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      if (rc == APSP_OK && (best < 0 || ms < tbest)) {
+      for (int r = 0; r < 3 && rc == APSP_OK; ++r) {
+        float m = 0;
+        rc = fill(mats, total, dtype, st);
+        if (rc == APSP_OK)
+          rc = time_on_stream(st, &m, [&] { return run_batched_direct(descs.data(), count, dtype, st, &dbuf, &dcap); });
+        if (rc == APSP_OK && (r == 0 || m < ms)) ms = m;
+      }
+      if (rc == APSP_OK && (best < 0 || ms < 0.99f * tbest)) {
         best = c;
         tbest = ms;
       }
@@ -212,20 +232,14 @@ extern "C" int apsp_autotune(int dtype, void *stream, char *report, int64_t repo
     for (int j = 0; j < 2 && rc == APSP_OK; ++j) {
       apsp_options o{};
       o.kblock = j ? 128 : 64;
-      o.flags = APSP_FLAG_NO_GRAPH;
-      cudaEvent_t e0, e1;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      rc = fill(m, (size_t)n * n, dtype, st);
-      if (rc == APSP_OK) rc = apsp_fw_ex(m, n, n, dtype, &o, st);  // warm-up (workspace, attributes)
-      if (rc == APSP_OK) rc = fill(m, (size_t)n * n, dtype, st);
-      cudaEventRecord(e0, st);
-      if (rc == APSP_OK) rc = apsp_fw_ex(m, n, n, dtype, &o, st);
-      cudaEventRecord(e1, st);
-      if (rc == APSP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms[j], e0, e1) != cudaSuccess))
-        rc = APSP_ECUDA;
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
+      // two warm-up calls (workspace, attributes, then the captured graph),
+      // then the best of 3 graph replays: the form a repeated solve takes
+      for (int r = 0; r < 5 && rc == APSP_OK; ++r) {
+        float t = 0;
+        rc = fill(m, (size_t)n * n, dtype, st);
+        if (rc == APSP_OK) rc = time_on_stream(st, &t, [&] { return apsp_fw_ex(m, n, n, dtype, &o, st); });
+        if (rc == APSP_OK && r >= 2 && (r == 2 || t < ms[j])) ms[j] = t;
+      }
     }
     cudaFree(m);
     if (rc != APSP_OK) return rc;
