@@ -305,7 +305,8 @@ def bench_batched(count: int = 4096, steps: int = 3, seed: int = 5):
             "ms_per_batch": t_batched * 1e3, "loop_graphs_per_s": count / t_loop,
             "loop_ms_per_batch": t_loop * 1e3, "speedup_vs_loop": t_loop / t_batched,
             "bit_exact_vs_loop": exact, "timing": "CUDA events, input restore (one device copy) included",
-            "autotuned_shapes": {str(b["n_max"]): b["best"] for b in tuning["batched"]}}
+            "autotuned_shapes": {str(b["n_max"]): v for b, v in zip(tuning["batched"], tuning["batch_variants"])},
+            "per_bucket_fastest_alone": {str(b["n_max"]): b["best"] for b in tuning["batched"]}}
 
 
 def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), server_factory=None,

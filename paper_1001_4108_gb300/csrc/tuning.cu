@@ -257,8 +257,9 @@ extern "C" int apsp_autotune(int dtype, void *stream, char *report, int64_t repo
     g_tab.kblock_cross[di] = cross;
     g_tab.tuned[di] = 1;
   }
-  char tail[96];
-  snprintf(tail, sizeof(tail), "], \"kblock_crossover\": %lld}", (long long)cross);
+  char tail[160];
+  snprintf(tail, sizeof(tail), "], \"kblock_crossover\": %lld, \"batch_variants\": [%d, %d, %d, %d, %d]}",
+           (long long)cross, best_v[0], best_v[1], best_v[2], best_v[3], best_v[4]);
   rep += tail;
   if (report && report_len > 0) {
     const size_t k = std::min<size_t>(rep.size(), (size_t)report_len - 1);
