@@ -300,10 +300,14 @@ def test_host_entry_point():
                                torch.cuda.current_stream().cuda_stream)
     np.testing.assert_array_equal(a[:, :333], exp)
     assert (a[:, 333:] == -7).all()
-    f = inputs.dense_f32(500, seed=3)
+    f = inputs.dense_f32(500, seed=3)  # rows padded to 504 on the device: pitched copies
     g = f.copy()
     binding.apsp_fw_host(g)
     assert_fp32_close(g, oracle.fw_f64(f))
+    h = inputs.int_graph(520, 0.1, 1, 1000, seed=4)  # n a multiple of 8: one linear copy each way
+    e = oracle.fw_int32_conv(h)
+    binding.apsp_fw_host(h)
+    np.testing.assert_array_equal(h, e)
 
 
 # ------------------------------------------------------- full size, sampled ---
