@@ -31,8 +31,17 @@ template <typename T, int S, int M>
 struct TileIO {
   using C = typename Arith<T>::C;
   static constexpr int LD = BShape<S, M>::LD;
+  // A tile entirely inside the matrix needs no masks (the common case).
   __device__ static void load(const T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, int ty, int tx,
                               C (&x)[M][M]) {
+    if (r0 + S <= n && c0 + S <= n) {
+      const T *p = d + (r0 + M * ty) * ld + c0 + M * tx;
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::load(p[a * ld + c]);
+      return;
+    }
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
@@ -43,6 +52,14 @@ struct TileIO {
   }
   __device__ static void store(T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, int ty, int tx,
                                const C (&x)[M][M], bool last) {
+    if (r0 + S <= n && c0 + S <= n) {
+      T *p = d + (r0 + M * ty) * ld + c0 + M * tx;
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int c = 0; c < M; ++c) p[a * ld + c] = last ? Arith<T>::finish(x[a][c]) : (T)x[a][c];
+      return;
+    }
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
@@ -59,27 +76,48 @@ struct TileIO {
   }
 };
 
+// Reinterprets a 32-bit word as the compute type (int32 or fp32).
+template <typename C> __device__ __forceinline__ C word_as(int v);
+template <> __device__ __forceinline__ int32_t word_as<int32_t>(int v) { return v; }
+template <> __device__ __forceinline__ float word_as<float>(int v) { return __int_as_float(v); }
+
 // acc[a][c] <- min(acc[a][c], min_k A[M ty + a][k] + B[k][M tx + c]) over the
-// tile's k's; A and B row-major in shared memory with the padded stride.
+// first 4 * kq_end k's of the tile (the k-block's vertices inside the graph,
+// rounded up: the padding k's hold infinity); A and B row-major in shared
+// memory with the padded stride.
 template <typename T, int S, int M>
 __device__ __forceinline__ void minplus_tile(typename Arith<T>::C (&acc)[M][M], const typename Arith<T>::C *A,
-                                             const typename Arith<T>::C *B, int ty, int tx) {
+                                             const typename Arith<T>::C *B, int ty, int tx, int kq_end) {
   using C = typename Arith<T>::C;
   constexpr int LD = BShape<S, M>::LD;
+  static_assert(sizeof(C) == 4 && (M == 2 || M == 4), "vector shared loads of 4-byte elements");
+  static_assert((LD * 4) % 16 == 0, "16-byte aligned rows");
 #pragma unroll 4
-  for (int kq = 0; kq < S / 4; ++kq) {
+  for (int kq = 0; kq < kq_end; ++kq) {
     C av[M][4];
 #pragma unroll
-    for (int a = 0; a < M; ++a) {
-      const C *p = A + (M * ty + a) * LD + 4 * kq;
-      av[a][0] = p[0]; av[a][1] = p[1]; av[a][2] = p[2]; av[a][3] = p[3];
+    for (int a = 0; a < M; ++a) {  // 4 k's of row M ty + a: one 128-bit load
+      const int4 v = *reinterpret_cast<const int4 *>(A + (M * ty + a) * LD + 4 * kq);
+      av[a][0] = word_as<C>(v.x);
+      av[a][1] = word_as<C>(v.y);
+      av[a][2] = word_as<C>(v.z);
+      av[a][3] = word_as<C>(v.w);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const C *q = B + (4 * kq + u) * LD + M * tx;
       C bv[M];
-#pragma unroll
-      for (int c = 0; c < M; ++c) bv[c] = q[c];
+      if constexpr (M == 4) {
+        const int4 v = *reinterpret_cast<const int4 *>(q);
+        bv[0] = word_as<C>(v.x);
+        bv[1] = word_as<C>(v.y);
+        bv[2] = word_as<C>(v.z);
+        bv[3] = word_as<C>(v.w);
+      } else {
+        const int2 v = *reinterpret_cast<const int2 *>(q);
+        bv[0] = word_as<C>(v.x);
+        bv[1] = word_as<C>(v.y);
+      }
 #pragma unroll
       for (int a = 0; a < M; ++a)
 #pragma unroll
@@ -117,6 +155,8 @@ __global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDe
     for (int b = 0; b < R; ++b) {
       const bool last = b == R - 1;
       const int64_t p0 = (int64_t)b * S;
+      const int kvalid = (int)min((int64_t)S, n - p0);  // vertices of k-block b inside the graph
+      const int kq_end = (kvalid + 3) / 4;
       // ---- phase 1: close the diagonal tile (registers + row/column k broadcast)
       C x[M][M];
       IO::load(d, ld, n, p0, p0, ty, tx, x);
@@ -126,7 +166,7 @@ __global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDe
       if (tx == 0)
 #pragma unroll
         for (int a = 0; a < M; ++a) colbuf[M * ty + a] = x[a][0];
-      for (int kq = 0; kq < Q; ++kq) {
+      for (int kq = 0; kq < (kvalid + M - 1) / M; ++kq) {
 #pragma unroll
         for (int u = 0; u < M; ++u) {
           const int k = M * kq + u;
@@ -164,9 +204,9 @@ __global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDe
         IO::to_smem(Ps, ty, tx, acc);
         __syncthreads();
         if (row)
-          minplus_tile<T, S, M>(acc, Ds, Ps, ty, tx);
+          minplus_tile<T, S, M>(acc, Ds, Ps, ty, tx, kq_end);
         else
-          minplus_tile<T, S, M>(acc, Ps, Ds, ty, tx);
+          minplus_tile<T, S, M>(acc, Ps, Ds, ty, tx, kq_end);
         IO::store(d, ld, n, r0, c0, ty, tx, acc, last);
         __syncthreads();
       }
@@ -183,7 +223,7 @@ __global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDe
           IO::load(d, ld, n, r0, c0, ty, tx, acc);
           IO::to_smem(Qs, ty, tx, bt);
           __syncthreads();
-          minplus_tile<T, S, M>(acc, Ps, Qs, ty, tx);
+          minplus_tile<T, S, M>(acc, Ps, Qs, ty, tx, kq_end);
           IO::store(d, ld, n, r0, c0, ty, tx, acc, last);
           __syncthreads();
         }
