@@ -99,7 +99,7 @@ struct SideEntry {
   cudaEvent_t fork, join;
   int prio;
 };
-constexpr size_t kMaxSide = 32;
+constexpr size_t kMaxSide = 256;
 std::vector<SideEntry> g_side;
 
 // Fills a->side, fork, join, side_prio (nullptr side: no lookahead).  Caller
@@ -114,7 +114,9 @@ void side_resources_locked(int dev, cudaStream_t stream, bool capturing, RunArgs
       a->side_prio = e.prio;
       return;
     }
-  if (capturing) return;
+  // Never evicted (another thread may be enqueueing on an entry right now):
+  // past kMaxSide launching streams, new ones run the plain schedule.
+  if (capturing || g_side.size() >= kMaxSide) return;
   int least = 0, greatest = 0;
   if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return;
   SideEntry e{dev, stream, nullptr, nullptr, nullptr, greatest};
@@ -124,12 +126,6 @@ void side_resources_locked(int dev, cudaStream_t stream, bool capturing, RunArgs
     if (e.fork) cudaEventDestroy(e.fork);
     cudaStreamDestroy(e.side);
     return;
-  }
-  if (g_side.size() >= kMaxSide) {  // released by CUDA once their work completes
-    cudaEventDestroy(g_side.front().fork);
-    cudaEventDestroy(g_side.front().join);
-    cudaStreamDestroy(g_side.front().side);
-    g_side.erase(g_side.begin());
   }
   g_side.push_back(e);
   a->side = e.side;

@@ -212,6 +212,36 @@ def test_lookahead_graph_replay_and_user_capture():
         np.testing.assert_array_equal(t.cpu().numpy(), exp)
 
 
+def test_lookahead_concurrent_streams():
+    # two host threads solving on their own streams at once: each launching
+    # stream has its own side stream, fork/join events and workspace
+    import threading
+    ws = [_graph("i32", 1100, seed=s) for s in (5, 6)]
+    exp = [oracle.fw_int32_conv(w) for w in ws]
+    errors = []
+
+    def worker(k):
+        try:
+            s = torch.cuda.Stream()
+            src = torch.from_numpy(ws[k]).cuda()
+            t = torch.empty_like(src)
+            for _ in range(3):  # direct, graph capture, replay
+                with torch.cuda.stream(s):
+                    t.copy_(src)
+                    binding.apsp_fw(t, stream=s)
+                s.synchronize()
+                np.testing.assert_array_equal(t.cpu().numpy(), exp[k])
+        except BaseException as e:  # reported by the main thread
+            errors.append(e)
+
+    th = [threading.Thread(target=worker, args=(k,)) for k in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not errors, errors
+
+
 def test_negative_cycle_flag():
     w = np.array([[0, 1, INF], [-3, 0, 1], [INF, INF, 0]], np.int32)
     t = torch.from_numpy(w).cuda()
