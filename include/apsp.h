@@ -90,6 +90,14 @@ typedef enum apsp_status {
                                      (same results, slower for fp32)                     */
 #define APSP_FLAG_NO_LOOKAHEAD 0x20 /* plain stage order: phases 1 and 2 of stage b+1 do
                                      not overlap phase 3 of stage b (same results)       */
+#define APSP_FLAG_VALIDATE   0x40 /* before solving, check the input against the value
+                                     conventions above (one pass over the matrix, then a
+                                     stream synchronize): int32 entries <= 2^29 and
+                                     (n-1)(Wmax+|Wmin|) < 2^28; int16 entries in
+                                     [0, 16383] and (n-1)Wmax < 16383; fp32 no NaN.
+                                     APSP_EINVAL if violated.  This flag and
+                                     APSP_FLAG_NEGCYCLE synchronize, so they are refused
+                                     (APSP_EINVAL) while the stream is being captured.  */
 
 typedef struct apsp_options {
     int32_t kblock;          /* k-block depth s (64 or 128); 0 = chosen from n and dtype */

@@ -2,7 +2,9 @@
 // the tile side, CUDA-graph replay of the stage loop, the host-buffer entry
 // point and the device error word.
 #include <algorithm>
+#include <climits>
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 #include <vector>
 
@@ -13,6 +15,8 @@
 static __device__ int g_apsp_err;
 // Set by the negative-cycle check.
 static __device__ int g_apsp_negcycle;
+// Input range of the validation pass: max finite entry, min entry, NaN seen.
+static __device__ int g_apsp_range[4];
 
 namespace apsp {
 
@@ -206,6 +210,66 @@ __global__ void diag_negative(const T *d, int64_t n, int64_t ld, int *flag) {
     if (d[i * ld + i] < (T)0) atomicExch(flag, 1);
 }
 
+// One pass over the matrix: the largest entry below the dtype's infinity,
+// the smallest entry, the largest entry overall and (fp32) whether a NaN
+// occurs.  int16 entries are compared as int32.  Rows by blockIdx.y, columns
+// by the threads of blockIdx.x (coalesced).
+template <typename T>
+__global__ void input_range(const T *d, int64_t n, int64_t ld, int inf, int *range) {
+  int mx = INT_MIN, mn = INT_MAX, top = INT_MIN, nan = 0;
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+      const T v = d[i * ld + j];
+      if constexpr (std::is_same<T, float>::value) {
+        nan |= v != v;
+      } else {
+        const int x = (int)v;
+        if (x < inf) mx = max(mx, x);
+        mn = min(mn, x);
+        top = max(top, x);
+      }
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+    nan |= __shfl_xor_sync(0xffffffffu, nan, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&range[0], mx);
+    atomicMin(&range[1], mn);
+    atomicMax(&range[2], top);
+    if (nan) atomicExch(&range[3], 1);
+  }
+}
+
+// APSP_FLAG_VALIDATE: the value conventions of the header (synchronizes).
+int validate_input(const void *dist, int64_t n, int64_t ld, int dtype, cudaStream_t st) {
+  int *range = nullptr;
+  if (cudaGetSymbolAddress(reinterpret_cast<void **>(&range), g_apsp_range) != cudaSuccess) return APSP_ECUDA;
+  static std::mutex mu;  // one validation at a time uses the device words
+  std::lock_guard<std::mutex> lk(mu);
+  const int init[4] = {INT_MIN, INT_MAX, INT_MIN, 0};
+  if (cudaMemcpyAsync(range, init, sizeof(init), cudaMemcpyHostToDevice, st) != cudaSuccess) return APSP_ECUDA;
+  const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 4), (unsigned)std::min<int64_t>(n, 2048));
+  if (dtype == APSP_I32)
+    input_range<int32_t><<<grid, 256, 0, st>>>((const int32_t *)dist, n, ld, 1 << 29, range);
+  if (dtype == APSP_F32) input_range<float><<<grid, 256, 0, st>>>((const float *)dist, n, ld, 0, range);
+  if (dtype == APSP_I16) input_range<int16_t><<<grid, 256, 0, st>>>((const int16_t *)dist, n, ld, 16383, range);
+  int h[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(h, range, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return APSP_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return APSP_ECUDA;
+  if (dtype == APSP_F32) return h[3] ? APSP_EINVAL : APSP_OK;
+  const int64_t wmax = h[0] == INT_MIN ? 0 : std::max(h[0], 0), wneg = h[1] < 0 ? -(int64_t)h[1] : 0;
+  if (dtype == APSP_I32) {
+    if (h[2] > (1 << 29)) return APSP_EINVAL;  // above infinity
+    return (n - 1) * (wmax + wneg) < (1 << 28) ? APSP_OK : APSP_EINVAL;
+  }
+  if (h[1] < 0) return APSP_EINVAL;  // int16: non-negative weights
+  if (h[2] > 16383) return APSP_EINVAL;
+  return (n - 1) * wmax < 16383 ? APSP_OK : APSP_EINVAL;
+}
+
 int check_negcycle(void *dist, int64_t n, int64_t ld, int dtype, cudaStream_t st, int *neg) {
   if (cudaMemsetAsync(neg, 0, sizeof(int), st) != cudaSuccess) return APSP_ECUDA;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
@@ -378,6 +442,12 @@ int solve(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt,
 
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(a.stream, &cap) != cudaSuccess) return APSP_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone && (a.flags & (APSP_FLAG_VALIDATE | APSP_FLAG_NEGCYCLE)))
+    return APSP_EINVAL;  // both synchronize the stream
+  if (a.flags & APSP_FLAG_VALIDATE) {
+    st = validate_input(dist, n, ld, dtype, a.stream);
+    if (st != APSP_OK) return st;
+  }
   const size_t need = (a.flags & APSP_FLAG_NO_WORKSPACE) ? 0 : workspace_bytes_for(n, dtype, a.S);
   if (need) {
     if (opt && opt->workspace) {

@@ -242,6 +242,54 @@ def test_lookahead_concurrent_streams():
     assert not errors, errors
 
 
+def _status(w, flags, n=None):
+    t = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+    n = w.shape[0] if n is None else n
+    opt = binding.Options(0, flags, None, 0, None, 0)
+    st = binding.apsp_fw_raw(t.data_ptr(), n, t.stride(0), binding.dtype_code(w.dtype),
+                             torch.cuda.current_stream().cuda_stream, opt)
+    torch.cuda.synchronize()
+    return st, t.cpu().numpy()
+
+
+def test_validate_flag():
+    F = binding.FLAG_VALIDATE
+    w = inputs.c1(seed=0)  # n = 1024, weights 1..1000: 1023 * 1000 < 2^28
+    st, d = _status(w, F)
+    assert st == binding.APSP_OK
+    np.testing.assert_array_equal(d, oracle.fw_int32_conv(w))
+    r = inputs.int_graph(700, 0.2, 0, 1000, seed=3, potential_max=50)  # negative weights within the bound
+    assert _status(r, F)[0] == binding.APSP_OK
+    for (i, j, v) in [(0, 1, 300000), (3, 4, (1 << 29) + 1), (5, 6, -300000)]:
+        bad = w.copy()
+        bad[i, j] = v
+        st, d = _status(bad, F)
+        assert st == binding.APSP_EINVAL, (i, j, v)
+        assert np.array_equal(d, bad), "a refused input must be left untouched"
+    h = inputs.to_int16(inputs.int_graph(500, 0.1, 1, 30, seed=4))  # 499 * 30 < 16383
+    assert _status(h, F)[0] == binding.APSP_OK
+    for v in (-1, 40, 20000):  # negative, over the bound, above infinity
+        bad = h.copy()
+        bad[2, 3] = v
+        assert _status(bad, F)[0] == binding.APSP_EINVAL, v
+    f = inputs.dense_f32(300, seed=2)
+    assert _status(f, F)[0] == binding.APSP_OK
+    bad = f.copy()
+    bad[7, 8] = np.nan
+    assert _status(bad, F)[0] == binding.APSP_EINVAL
+    # synchronizing flags are refused inside a stream capture
+    t = torch.from_numpy(w).cuda()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    codes = []
+    with torch.cuda.graph(g, stream=s):
+        opt = binding.Options(0, F, None, 0, None, 0)
+        codes.append(binding.apsp_fw_raw(t.data_ptr(), 1024, 1024, binding.APSP_I32, s.cuda_stream, opt))
+        opt = binding.Options(0, binding.FLAG_NEGCYCLE, None, 0, None, 0)
+        codes.append(binding.apsp_fw_raw(t.data_ptr(), 1024, 1024, binding.APSP_I32, s.cuda_stream, opt))
+    assert codes == [binding.APSP_EINVAL, binding.APSP_EINVAL]
+
+
 def test_negative_cycle_flag():
     w = np.array([[0, 1, INF], [-3, 0, 1], [INF, INF, 0]], np.int32)
     t = torch.from_numpy(w).cuda()
