@@ -390,11 +390,13 @@ def test_host_entry_point():
 
 # ------------------------------------------------------- full size, sampled ---
 
-@pytest.mark.parametrize("dt", ["f32", "i32"])
-def test_full_size_16384_sampled(dt):
-    """n = 16384 in the bench's configuration: sampled rows against Dijkstra
-    (exact), sampled triangle-inequality triples and Bellman rows."""
-    n = 16384
+@pytest.mark.parametrize("dt,n", [("f32", 16384), ("i32", 16384), ("f32", 32768)])
+def test_full_size_sampled(dt, n):
+    """The bench's size (and the largest complete fp32 graph, n = 32768, 4 GiB):
+    sampled rows against Dijkstra (exact), the Bellman equation
+    d_ij = min(w_ij, min_k w_ik + d_kj) on sampled rows (with d_ii = 0 it
+    holds only for the shortest-path matrix), and the triangle inequality on
+    10^6 sampled triples."""
     if dt == "f32":
         w = inputs.dense_f32(n, seed=0)
     else:
@@ -403,7 +405,7 @@ def test_full_size_16384_sampled(dt):
     binding.apsp_fw(t)
     torch.cuda.synchronize()
     g = inputs.rng(77)
-    rows = g.choice(n, size=6, replace=False)
+    rows = g.choice(n, size=6 if n <= 16384 else 3, replace=False)
     d_rows = t[torch.from_numpy(rows).cuda()].cpu().numpy()
     if dt == "f32":
         exact = oracle.dijkstra_rows_f32(w, rows)
@@ -411,6 +413,28 @@ def test_full_size_16384_sampled(dt):
     else:
         exact = oracle.dijkstra_rows_i32(w, rows)
         np.testing.assert_array_equal(d_rows, exact)
+    # Bellman equation on two rows, in FP64 / int64 on the device (a checker, not the product)
+    wt = torch.from_numpy(w).cuda()
+    for i in rows[:2]:
+        best = wt[i].double() if dt == "f32" else wt[i].long()
+        for k0 in range(0, n, 1024):
+            wk = wt[i, k0:k0 + 1024]
+            dk = t[k0:k0 + 1024]
+            if dt == "f32":
+                cand = (wk.double()[:, None] + dk.double()).min(0).values
+            else:
+                fin = (wk < inputs.INF_I32)[:, None] & (dk < (1 << 28))
+                cand = torch.where(fin, wk.long()[:, None] + dk.long(), torch.full_like(dk, 1 << 40, dtype=torch.long))
+                cand = cand.min(0).values
+            best = torch.minimum(best, cand)
+        di = t[i].double() if dt == "f32" else t[i].long()
+        if dt == "f32":
+            assert torch.all((di - best).abs() <= 1e-5 * best.abs()).item()  # weights > 0: S_ij = d_ij
+        else:
+            best = torch.where(best >= (1 << 28), torch.full_like(best, inputs.INF_I32), best)
+            best[i] = 0
+            assert torch.equal(di, best)
+    del wt
     # triangle inequality on 10^6 random triples (within fp32 rounding)
     i = torch.from_numpy(g.integers(0, n, 1_000_000)).cuda()
     j = torch.from_numpy(g.integers(0, n, 1_000_000)).cuda()
