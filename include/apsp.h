@@ -90,6 +90,14 @@ typedef enum apsp_status {
                                      (same results, slower for fp32)                     */
 #define APSP_FLAG_NO_LOOKAHEAD 0x20 /* plain stage order: phases 1 and 2 of stage b+1 do
                                      not overlap phase 3 of stage b (same results)       */
+#define APSP_FLAG_NARROW     0x80 /* APSP_I32 only: the caller states that every weight is
+                                     >= 0 and (n-1)*Wmax < 16383 (APSP_FLAG_VALIDATE then
+                                     checks exactly that); the matrix is copied to int16,
+                                     solved by the packed int16x2 kernels (about twice the
+                                     rate) and copied back, with absent = 2^29 in and out.
+                                     Same results as the int32 path.  Uses library memory
+                                     (n^2 x 2 bytes + int16 panels, per device and stream);
+                                     APSP_EINVAL with a caller workspace or apsp_fw_paths. */
 #define APSP_FLAG_VALIDATE   0x40 /* before solving, check the input against the value
                                      conventions above (one pass over the matrix, then a
                                      stream synchronize): int32 entries <= 2^29 and

@@ -21,6 +21,7 @@ APSP_ETIMEOUT, APSP_EBUSY, APSP_EPENDING, APSP_ENEGCYCLE = 5, 6, 7, 8
 FLAG_NO_GRAPH, FLAG_GENERIC, FLAG_REVERSE_K, FLAG_NEGCYCLE, FLAG_NO_WORKSPACE = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_NO_LOOKAHEAD = 0x20
 FLAG_VALIDATE = 0x40
+FLAG_NARROW = 0x80
 EVENTS_PER_STAGE = 5
 INF_I32 = 1 << 29
 INF_I16 = 16383

@@ -244,7 +244,7 @@ __global__ void input_range(const T *d, int64_t n, int64_t ld, int inf, int *ran
 }
 
 // APSP_FLAG_VALIDATE: the value conventions of the header (synchronizes).
-int validate_input(const void *dist, int64_t n, int64_t ld, int dtype, cudaStream_t st) {
+int validate_input(const void *dist, int64_t n, int64_t ld, int dtype, cudaStream_t st, bool narrow = false) {
   int *range = nullptr;
   if (cudaGetSymbolAddress(reinterpret_cast<void **>(&range), g_apsp_range) != cudaSuccess) return APSP_ECUDA;
   static std::mutex mu;  // one validation at a time uses the device words
@@ -261,6 +261,10 @@ int validate_input(const void *dist, int64_t n, int64_t ld, int dtype, cudaStrea
   if (cudaStreamSynchronize(st) != cudaSuccess) return APSP_ECUDA;
   if (dtype == APSP_F32) return h[3] ? APSP_EINVAL : APSP_OK;
   const int64_t wmax = h[0] == INT_MIN ? 0 : std::max(h[0], 0), wneg = h[1] < 0 ? -(int64_t)h[1] : 0;
+  if (dtype == APSP_I32 && narrow) {  // the int16 rules on int32 input
+    if (h[2] > (1 << 29) || h[1] < 0) return APSP_EINVAL;
+    return (n - 1) * wmax < 16383 ? APSP_OK : APSP_EINVAL;
+  }
   if (dtype == APSP_I32) {
     if (h[2] > (1 << 29)) return APSP_EINVAL;  // above infinity
     return (n - 1) * (wmax + wneg) < (1 << 28) ? APSP_OK : APSP_EINVAL;
@@ -268,6 +272,26 @@ int validate_input(const void *dist, int64_t n, int64_t ld, int dtype, cudaStrea
   if (h[1] < 0) return APSP_EINVAL;  // int16: non-negative weights
   if (h[2] > 16383) return APSP_EINVAL;
   return (n - 1) * wmax < 16383 ? APSP_OK : APSP_EINVAL;
+}
+
+// int32 <-> int16 copies of the narrowed solve (APSP_FLAG_NARROW).  Inputs
+// obey the int16 bound, so every entry is either < 16383 or absent (2^29).
+__global__ void narrow_i32(const int32_t *src, int64_t n, int64_t ld, int16_t *dst, int64_t ld16) {
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+      const int32_t v = src[i * ld + j];
+      dst[i * ld16 + j] = (int16_t)(v >= 16383 ? 16383 : v);
+    }
+}
+__global__ void widen_i16(const int16_t *src, int64_t ld16, int64_t n, int32_t *dst, int64_t ld) {
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+      const int32_t v = src[i * ld16 + j];
+      dst[i * ld + j] = v >= 16383 ? (1 << 29) : v;
+    }
+}
+dim3 rows_grid(int64_t n) {
+  return dim3((unsigned)std::min<int64_t>((n + 255) / 256, 4), (unsigned)std::min<int64_t>(n, 4096));
 }
 
 int check_negcycle(void *dist, int64_t n, int64_t ld, int dtype, cudaStream_t st, int *neg) {
@@ -444,9 +468,45 @@ int solve(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt,
   if (cudaStreamIsCapturing(a.stream, &cap) != cudaSuccess) return APSP_ECUDA;
   if (cap != cudaStreamCaptureStatusNone && (a.flags & (APSP_FLAG_VALIDATE | APSP_FLAG_NEGCYCLE)))
     return APSP_EINVAL;  // both synchronize the stream
+  const bool narrow = dtype == APSP_I32 && (a.flags & APSP_FLAG_NARROW);
+  if (narrow && (via || (opt && opt->workspace))) return APSP_EINVAL;
   if (a.flags & APSP_FLAG_VALIDATE) {
-    st = validate_input(dist, n, ld, dtype, a.stream);
+    st = validate_input(dist, n, ld, dtype, a.stream, narrow);
     if (st != APSP_OK) return st;
+  }
+  if (narrow) {
+    // int32 in and out, solved as int16x2 in a library buffer:
+    // [n x ld16 int16 copy][int16 panel workspace]
+    const int64_t ld16 = (n + 7) / 8 * 8;
+    const int S16 = choose_kblock(n, APSP_I16, opt ? opt->kblock : 0);
+    const size_t copy_bytes = ((size_t)n * ld16 * 2 + 255) / 256 * 256;
+    const size_t ws16 = workspace_bytes_for(n, APSP_I16, S16);
+    size_t got = 0;
+    char *buf = static_cast<char *>(
+        library_workspace(dev, a.stream, copy_bytes + ws16, cap != cudaStreamCaptureStatusNone, &got));
+    if (buf) {  // else (first use inside a capture): the int32 path, same result
+      narrow_i32<<<rows_grid(n), 256, 0, a.stream>>>(static_cast<const int32_t *>(dist), n, ld,
+                                                      reinterpret_cast<int16_t *>(buf), ld16);
+      RunArgs b = a;
+      b.d = buf;
+      b.ld = ld16;
+      b.S = S16;
+      b.tma_ok = true;  // 256-byte aligned buffer, 16-byte rows
+      b.ws = ws16 ? buf + copy_bytes : nullptr;
+      b.ws_bytes = ws16 ? got - copy_bytes : 0;
+      if (!(b.flags & APSP_FLAG_NO_LOOKAHEAD)) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        side_resources_locked(dev, b.stream, cap != cudaStreamCaptureStatusNone, &b);
+      }
+      const bool direct = (b.flags & APSP_FLAG_NO_GRAPH) || b.events || cap != cudaStreamCaptureStatusNone;
+      st = direct ? run_dtype(b, APSP_I16) : launch_with_graph(b, APSP_I16, dev);
+      if (st != APSP_OK) return st;
+      widen_i16<<<rows_grid(n), 256, 0, a.stream>>>(reinterpret_cast<const int16_t *>(buf), ld16, n,
+                                                     static_cast<int32_t *>(dist), ld);
+      if (cudaPeekAtLastError() != cudaSuccess) return APSP_ECUDA;
+      if (a.flags & APSP_FLAG_NEGCYCLE) return check_negcycle(dist, n, ld, dtype, a.stream, neg);
+      return APSP_OK;
+    }
   }
   const size_t need = (a.flags & APSP_FLAG_NO_WORKSPACE) ? 0 : workspace_bytes_for(n, dtype, a.S);
   if (need) {

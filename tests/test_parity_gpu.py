@@ -290,6 +290,35 @@ def test_validate_flag():
     assert codes == [binding.APSP_EINVAL, binding.APSP_EINVAL]
 
 
+def test_narrow_int32_through_int16():
+    # APSP_FLAG_NARROW: int32 in and out, solved by the int16x2 kernels;
+    # identical to the int32 path and the oracle
+    N, V = binding.FLAG_NARROW, binding.FLAG_VALIDATE
+    w32, _ = inputs.c3(seed=1)  # n = 2048, weights 1..7: 2047 * 7 < 16383
+    exp = oracle.fw_int32_conv(w32)
+    for flags in (N, N | V, N | binding.FLAG_NO_GRAPH, N | binding.FLAG_NO_LOOKAHEAD):
+        np.testing.assert_array_equal(gpu_solve(w32, flags=flags), exp)
+    src = torch.from_numpy(w32).cuda()
+    t = torch.empty_like(src)
+    for _ in range(3):  # direct, captured graph, replay
+        t.copy_(src)
+        binding.apsp_fw(t, flags=N)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(t.cpu().numpy(), exp)
+    # ragged n, padded leading dimension, unreachable pairs
+    w = inputs.int_graph(1001, 0.01, 1, 16, seed=8, ld=1004)
+    out = gpu_solve(w, 1001, flags=N)
+    np.testing.assert_array_equal(out[:, :1001], oracle.fw_int32_conv(np.ascontiguousarray(w[:, :1001])))
+    assert (out[:, 1001:] == -7).all()
+    # inputs outside the int16 rules are refused with the check, left untouched
+    for bad in (inputs.c1(seed=0), inputs.int_graph(300, 0.2, 0, 10, seed=1, potential_max=3)):
+        st, d = _status(bad, N | V)
+        assert st == binding.APSP_EINVAL and np.array_equal(d, bad)
+    via = torch.empty((2048, 2048), dtype=torch.int16, device="cuda")
+    with pytest.raises(binding.ApspError):
+        binding.apsp_fw_paths(torch.from_numpy(w32).cuda(), via, flags=N)
+
+
 def test_negative_cycle_flag():
     w = np.array([[0, 1, INF], [-3, 0, 1], [INF, INF, 0]], np.int32)
     t = torch.from_numpy(w).cuda()
