@@ -348,6 +348,16 @@ APSP_API int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_config
 APSP_API int apsp_device_error(int reset);
 
 /*
+ * Self-test of that failure path: enqueues one warp that waits on a barrier
+ * phase nothing completes, gives up after limit_ns nanoseconds (1 ns .. 10 s)
+ * and sets the device error word, exactly as a kernel's bounded wait does.
+ * No fault and no hang: afterwards apsp_device_error() returns the timeout
+ * code (1) and the context is usable.  APSP_EINVAL for a limit outside the
+ * range.  (Not part of the paper: tests the library's own error plumbing.)
+ */
+APSP_API int apsp_selftest_wait(int64_t limit_ns, void *stream);
+
+/*
  * Roofline calibration: runs the phase-3 inner loop of one instruction form on
  * every SM, with operands loaded from shared memory at every k step as in the
  * kernels (256 threads, 8 x 8 register micro-tile, a 32-k slice swept `iters`

@@ -31,7 +31,7 @@ EXPORTS = ["apsp_status_str", "apsp_version", "apsp_fw", "apsp_fw_ex", "apsp_fw_
            "apsp_workspace_bytes", "apsp_query_config", "apsp_device_error", "apsp_ubench_minplus",
            "apsp_fw_f32_noalloc", "apsp_fw_batched", "apsp_autotune", "apsp_tuning_save",
            "apsp_tuning_load", "apsp_server_create", "apsp_submit", "apsp_poll", "apsp_wait",
-           "apsp_server_stats", "apsp_server_destroy", "apsp_fw_paths", "apsp_path"]
+           "apsp_server_stats", "apsp_server_destroy", "apsp_fw_paths", "apsp_path", "apsp_selftest_wait"]
 
 
 class Options(ctypes.Structure):
@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
             L.apsp_workspace_bytes.argtypes = [i64, i32, ctypes.c_int32]
             L.apsp_workspace_bytes.restype = i64
             L.apsp_device_error.argtypes = [i32]
+            L.apsp_selftest_wait.argtypes = [i64, vp]
             L.apsp_ubench_minplus.argtypes = [i32, i64, i32, i32, vp, vp, ctypes.POINTER(ctypes.c_double)]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i32

@@ -110,15 +110,26 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Waits for the given phase of an mbarrier; gives up after kWaitLimitNs and
+// Waits for the given phase of an mbarrier; gives up after limit_ns and
 // returns false instead of hanging.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
+}
+
+// After a wait gave up at slice s of a ring of `stages` mbarriers: records
+// the error and waits (bounded again) for the copies this CTA still has in
+// flight -- slices s .. min(s + stages, nsl) - 1 -- so that none lands in
+// shared memory after the CTA has left.  Called by the thread that issued
+// the copies.
+__device__ __forceinline__ void give_up_and_drain(int *err, uint64_t *full, int s, int stages, int nsl) {
+  atomicCAS(err, 0, (int)kDevTimeoutTma);
+  for (int t = s; t < s + stages && t < nsl; ++t) mbar_wait_bounded(&full[t % stages], (t / stages) & 1);
 }
 
 // 2-D tiled TMA load global -> shared, completion counted on an mbarrier.

@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     }
     // every thread is done with stage st: refill it with slice s + STAGES
     if (__syncthreads_or(timed_out)) {
-      if (tid == 0) atomicCAS(err, 0, (int)kDevTimeoutTma);
+      if (tid == 0) give_up_and_drain(err, full, s, P::STAGES, P::NSL);
       return;
     }
     if (tid == 0 && s + P::STAGES < P::NSL) {
@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
         }
     }
     if (__syncthreads_or(timed_out)) {
-      if (tid == 0) atomicCAS(err, 0, (int)kDevTimeoutTma);
+      if (tid == 0) give_up_and_drain(err, full, s, P::STAGES, P::NSL);
       return;
     }
     if (tid == 0 && s + P::STAGES < P::NSL) {
@@ -876,7 +876,10 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
       }
     }
     if (__syncthreads_or(timed_out)) {
-      if (tid == 0) atomicCAS(err, 0, (int)kDevTimeoutTma);
+      if (tid == 0) {
+        give_up_and_drain(err, full, s, P::STAGES, P::NSL);
+        if (DEFER_C) mbar_wait_bounded(cbar, 0);
+      }
       return;
     }
     if (tid == 0 && s + P::STAGES < P::NSL) issue(s + P::STAGES, st);
@@ -884,7 +887,7 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
 
   if (DEFER_C) {
     // fold in the C tile (rows ty + G r, int16 columns 8 tx .. 8 tx + 7)
-    if (__syncthreads_or(!mbar_wait_bounded(cbar, 0))) {
+    if (__syncthreads_or(!mbar_wait_bounded(cbar, 0))) {  // all slices were consumed: only C is in flight
       if (tid == 0) atomicCAS(err, 0, (int)kDevTimeoutTma);
       return;
     }

@@ -319,6 +319,18 @@ def test_narrow_int32_through_int16():
         binding.apsp_fw_paths(torch.from_numpy(w32).cuda(), via, flags=N)
 
 
+def test_bounded_wait_gives_up_without_fault():
+    # a wait on a barrier phase that nothing completes runs out after 5 ms,
+    # sets the device error word and returns; the context stays usable
+    assert binding.device_error() == 0
+    assert binding.lib().apsp_selftest_wait(5_000_000, None) == binding.APSP_OK
+    assert binding.lib().apsp_device_error(1) == 1  # kDevTimeoutTma, then cleared
+    assert binding.device_error() == 0
+    w = inputs.c1(seed=2, n=600)
+    np.testing.assert_array_equal(gpu_solve(w), oracle.fw_int32_conv(w))
+    assert binding.lib().apsp_selftest_wait(0, None) == binding.APSP_EINVAL
+
+
 def test_negative_cycle_flag():
     w = np.array([[0, 1, INF], [-3, 0, 1], [INF, INF, 0]], np.int32)
     t = torch.from_numpy(w).cuda()
