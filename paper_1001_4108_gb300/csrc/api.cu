@@ -151,9 +151,12 @@ struct GraphKey {
   void *ws;
   void *via;
   int64_t via_ld;
+  const void *first_src;
+  void *last_dst;
   bool operator==(const GraphKey &o) const {
     return d == o.d && n == o.n && ld == o.ld && dtype == o.dtype && S == o.S && flags == o.flags &&
-           dev == o.dev && stream == o.stream && ws == o.ws && via == o.via && via_ld == o.via_ld;
+           dev == o.dev && stream == o.stream && ws == o.ws && via == o.via && via_ld == o.via_ld &&
+           first_src == o.first_src && last_dst == o.last_dst;
   }
 };
 struct GraphEntry {
@@ -167,7 +170,8 @@ std::vector<GraphKey> g_seen;
 cudaStream_t g_capture_stream[kMaxDev];
 
 int launch_with_graph(const RunArgs &a, int dtype, int dev) {
-  const GraphKey key{a.d, a.n, a.ld, dtype, a.S, a.flags, dev, a.stream, a.ws, a.via, a.via_ld};
+  const GraphKey key{a.d, a.n, a.ld, dtype, a.S, a.flags, dev, a.stream, a.ws, a.via, a.via_ld, a.first_src,
+                     a.last_dst};
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto &g : g_graphs)
     if (g.key == key) return cudaGraphLaunch(g.exec, a.stream) == cudaSuccess ? APSP_OK : APSP_ECUDA;
@@ -439,7 +443,8 @@ namespace apsp {
 namespace {
 // apsp_fw_ex, optionally with the path bookkeeping of apsp_fw_paths.
 int solve(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt, void *stream, int16_t *via,
-          int64_t via_ld) {
+          int64_t via_ld, const void *first_src = nullptr, int64_t first_src_ld = 0, void *last_dst = nullptr,
+          int64_t last_dst_ld = 0) {
   int st = check_args(dist, n, ld, dtype, opt);
   if (st != APSP_OK) return st;
   if (n == 0) return APSP_OK;
@@ -461,6 +466,10 @@ int solve(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt,
   a.err = err;
   a.via = via;
   a.via_ld = via_ld;
+  a.first_src = first_src;
+  a.first_src_ld = first_src_ld;
+  a.last_dst = last_dst;
+  a.last_dst_ld = last_dst_ld;
   const size_t es = (size_t)elem_size(dtype);
   a.tma_ok = (reinterpret_cast<uintptr_t>(dist) % 16 == 0) && ((size_t)ld * es) % 16 == 0;
 
@@ -608,10 +617,38 @@ extern "C" int apsp_fw_host(void *host_dist, int64_t n, int64_t ld, int dtype, v
     hs.bytes = bytes;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t row = (size_t)n * es, hpitch = (size_t)ld * es, dpitch = (size_t)dld * es;
+  char *hb = static_cast<char *>(host_dist), *db = static_cast<char *>(hs.buf);
+  // Pinned (device-mapped) host memory: the first stage's phase 3 reads its
+  // tiles from it and the last stage's phase 3 writes them back, so only the
+  // first stage's panels go in and the last stage's panels come out as
+  // copies.  Otherwise: the whole matrix each way.
+  const int S = choose_kblock(n, dtype, 0);
+  cudaPointerAttributes pa{};
+  const bool mapped = cudaPointerGetAttributes(&pa, host_dist) == cudaSuccess &&
+                      pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr;
+  // the kernels move C rows in 16-byte vectors: 16-byte aligned rows only
+  const bool aligned = reinterpret_cast<uintptr_t>(pa.devicePointer) % 16 == 0 && hpitch % 16 == 0;
+  if (mapped && aligned && (dtype == APSP_F32 || dtype == APSP_I32) && n % S == 0 && n > S) {
+    const int64_t pb = n - S;  // first row / column of the last block
+    cudaError_t e = cudaMemcpy2DAsync(db, dpitch, hb, hpitch, row, S, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(db + S * dpitch, dpitch, hb + S * hpitch, hpitch, S * es, n - S,
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return APSP_ECUDA;
+    st = solve(hs.buf, n, dld, dtype, nullptr, stream, nullptr, 0, pa.devicePointer, ld, pa.devicePointer, ld);
+    if (st == APSP_OK) {
+      e = cudaMemcpy2DAsync(hb + pb * hpitch, hpitch, db + pb * dpitch, dpitch, row, S, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(hb + pb * es, hpitch, db + pb * es, dpitch, S * es, pb, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return APSP_ECUDA;
+      return cudaStreamSynchronize(s) == cudaSuccess ? APSP_OK : APSP_ECUDA;
+    }
+    if (st != APSP_EUNSUPPORTED) return st;  // else: the copying form below
+  }
   // one linear copy each way when the rows are contiguous on both sides (a
   // pitched copy of n rows moves the same bytes at a fraction of the rate)
   const bool linear = ld == dld;
-  const size_t row = (size_t)n * es, hpitch = (size_t)ld * es, dpitch = (size_t)dld * es;
   cudaError_t e = linear ? cudaMemcpyAsync(hs.buf, host_dist, bytes, cudaMemcpyHostToDevice, s)
                          : cudaMemcpy2DAsync(hs.buf, dpitch, host_dist, hpitch, row, n, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return APSP_ECUDA;

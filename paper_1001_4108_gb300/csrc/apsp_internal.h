@@ -29,6 +29,15 @@ struct RunArgs {
   // improvement of d_ij (nullptr = off).
   int16_t *via;
   int64_t via_ld;
+  // Optional routing of the C tiles of phase 3 (host entry point): stage 0
+  // reads them from first_src and the last stage writes them to last_dst,
+  // both device-accessible host memory with their own leading dimensions
+  // (nullptr = the matrix).  Needs whole tiles and the TMA kernels; a run
+  // that cannot honor it returns APSP_EUNSUPPORTED before enqueueing work.
+  const void *first_src;
+  int64_t first_src_ld;
+  void *last_dst;
+  int64_t last_dst_ld;
 };
 
 // Events a traced solve records per stage (apsp_options.events).

@@ -231,6 +231,14 @@ static int run_rounds(const RunArgs &a) {
   if constexpr (std::is_same<T, int16_t>::value) p3_tma = use_s16;
   else p3_tma = use_tma;
   const bool needs_panel = use_packed || use_s16;
+  const bool routed = a.first_src || a.last_dst;
+  const auto aligned16 = [](const void *p, int64_t ld_) {
+    return reinterpret_cast<uintptr_t>(p) % 16 == 0 && ((size_t)ld_ * sizeof(T)) % 16 == 0;
+  };
+  if (routed && (ragged || R < 2 || !p3_tma || std::is_same<T, int16_t>::value ||
+                 (a.first_src && !aligned16(a.first_src, a.first_src_ld)) ||
+                 (a.last_dst && !aligned16(a.last_dst, a.last_dst_ld))))
+    return APSP_EUNSUPPORTED;
   const bool lookahead = p3_tma && a.side && !(a.flags & APSP_FLAG_NO_LOOKAHEAD) && R >= kLookaheadMinRounds &&
                          (!needs_panel || nbuf == 2);
   auto buf_of = [&](int b) { return lookahead ? (b & 1) : 0; };
@@ -261,8 +269,9 @@ static int run_rounds(const RunArgs &a) {
     T *bpb = (use_packed && full_k(b)) ? bp[buf_of(b)] : nullptr;
     if constexpr (HAS_TMA) {
       if (use_tma && full_k(b))
-        return launch(fw_tile_tma<T, S, 1, VIA>, g, P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB, d, n, ld, b, R,
-                      TileSet{}, last, reverse, bpb, 2 * np, a.via, a.via_ld, a.err);
+        return launch(fw_tile_tma<T, S, 1, VIA>, g, P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB,
+                      CRoute<T>{d, ld, d, ld}, n, b, R, TileSet{}, last, reverse, bpb, 2 * np, a.via, a.via_ld,
+                      a.err);
     }
     return launch(fw_phase2<T, S, K::NT2>, g, K::NT2, K::SM2, s, prio, d, n, ld, b, R, last, bpb, 2 * np, a.via,
                   a.via_ld);
@@ -271,6 +280,15 @@ static int run_rounds(const RunArgs &a) {
   auto phase3 = [&](int b, int kind, cudaStream_t s, int prio) -> cudaError_t {
     if (R == 1) return cudaSuccess;
     const int last = b == R - 1 ? 1 : 0;
+    CRoute<T> cr{d, ld, d, ld};
+    if (b == 0 && a.first_src) {
+      cr.src = static_cast<const T *>(a.first_src);
+      cr.src_ld = a.first_src_ld;
+    }
+    if (last && a.last_dst) {
+      cr.dst = static_cast<T *>(a.last_dst);
+      cr.dst_ld = a.last_dst_ld;
+    }
     if (full_k(b)) {
       if constexpr (std::is_same<T, int16_t>::value) {
         if (use_s16) {
@@ -289,15 +307,15 @@ static int run_rounds(const RunArgs &a) {
           const TileSet te = make_tileset(kind, kPartEdge, b, R, ragged);
           cudaError_t e = cudaSuccess;
           if (ti.total() > 0)
-            e = reverse ? launch(fw_phase3_f32x2<S, true, true, VIA>, dim3(ti.total()), tpb, sm, s, prio, mA, mb, d,
-                                 n, ld, b, ti, a.via, a.via_ld, a.err)
-                        : launch(fw_phase3_f32x2<S, false, true, VIA>, dim3(ti.total()), tpb, sm, s, prio, mA, mb, d,
-                                 n, ld, b, ti, a.via, a.via_ld, a.err);
+            e = reverse ? launch(fw_phase3_f32x2<S, true, true, VIA>, dim3(ti.total()), tpb, sm, s, prio, mA, mb,
+                                 cr, n, b, ti, a.via, a.via_ld, a.err)
+                        : launch(fw_phase3_f32x2<S, false, true, VIA>, dim3(ti.total()), tpb, sm, s, prio, mA, mb,
+                                 cr, n, b, ti, a.via, a.via_ld, a.err);
           if (e == cudaSuccess && te.total() > 0)
-            e = reverse ? launch(fw_phase3_f32x2<S, true, false, VIA>, dim3(te.total()), tpb, sm, s, prio, mA, mb, d,
-                                 n, ld, b, te, a.via, a.via_ld, a.err)
-                        : launch(fw_phase3_f32x2<S, false, false, VIA>, dim3(te.total()), tpb, sm, s, prio, mA, mb, d,
-                                 n, ld, b, te, a.via, a.via_ld, a.err);
+            e = reverse ? launch(fw_phase3_f32x2<S, true, false, VIA>, dim3(te.total()), tpb, sm, s, prio, mA, mb,
+                                 cr, n, b, te, a.via, a.via_ld, a.err)
+                        : launch(fw_phase3_f32x2<S, false, false, VIA>, dim3(te.total()), tpb, sm, s, prio, mA, mb,
+                                 cr, n, b, te, a.via, a.via_ld, a.err);
           return e;
         }
       }
@@ -305,8 +323,8 @@ static int run_rounds(const RunArgs &a) {
         if (use_tma) {
           const TileSet ts = make_tileset(kind, kPartAny, b, R, ragged);
           if (ts.total() == 0) return cudaSuccess;
-          return launch(fw_tile_tma<T, S, 0, VIA>, dim3(ts.total()), P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB, d,
-                        n, ld, b, R, ts, last, reverse, (T *)nullptr, (int64_t)0, a.via, a.via_ld, a.err);
+          return launch(fw_tile_tma<T, S, 0, VIA>, dim3(ts.total()), P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB, cr,
+                        n, b, R, ts, last, reverse, (T *)nullptr, (int64_t)0, a.via, a.via_ld, a.err);
         }
       }
     }

@@ -34,6 +34,19 @@ __device__ __forceinline__ void note_via(int16_t *via, int64_t via_ld, int64_t i
   if (now < before) via[i * via_ld + j] = (int16_t)b;
 }
 
+// Where a phase-3 launch reads and writes its C tiles: normally the matrix
+// itself (src = dst = d).  The host entry point can point the first stage's
+// reads at the caller's host matrix and the last stage's writes back to it,
+// so that the matrix crosses the host link inside those two stages instead
+// of in separate copies.  The panels always come from the device matrix.
+template <typename T>
+struct CRoute {
+  const T *src;
+  int64_t src_ld;
+  T *dst;
+  int64_t dst_ld;
+};
+
 // ------------------------------------------------------------------ phase 1
 // One CTA closes the diagonal tile (b, b): s sequential k steps, each a rank-1
 // update x_ij <- min(x_ij, x_ik + x_kj) of the whole tile.
@@ -353,7 +366,7 @@ __device__ __forceinline__ void lds4(const T *p, T &x0, T &x1, T &x2, T &x3) {
 template <typename T, int S, int MODE, bool VIA = false>
 __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     fw_tile_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                T *__restrict__ d, int64_t n, int64_t ld, int b, int R, const TileSet ts, int last, int reverse,
+                const CRoute<T> cr, int64_t n, int b, int R, const TileSet ts, int last, int reverse,
                 T *__restrict__ bp, int64_t bp_ld, int16_t *__restrict__ via, int64_t via_ld, int *err) {
   using P = P3Tma<S>;
   constexpr int G = P::G;
@@ -405,7 +418,7 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
   if (full_tile) {
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const T *row = d + (I0 + ty + G * r) * ld + J0 + 4 * tx;
+      const T *row = cr.src + (I0 + ty + G * r) * cr.src_ld + J0 + 4 * tx;
 #pragma unroll
       for (int h = 0; h < 2; ++h)
         ld4<T>(row + h * (S / 2), acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
@@ -416,7 +429,7 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int64_t gi = I0 + ty + G * r, gj = J0 + (c / 4) * (S / 2) + 4 * tx + (c % 4);
-        acc[r][c] = (gi < n && gj < n) ? d[gi * ld + gj] : Arith<T>::inf();
+        acc[r][c] = (gi < n && gj < n) ? cr.src[gi * cr.src_ld + gj] : Arith<T>::inf();
       }
   }
 
@@ -500,13 +513,13 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int64_t gi = I0 + ty + G * r, gj = J0 + (c / 4) * (S / 2) + 4 * tx + (c % 4);
-        if (gi < n && gj < n) note_via(via, via_ld, gi, gj, acc[r][c], d[gi * ld + gj], b);
+        if (gi < n && gj < n) note_via(via, via_ld, gi, gj, acc[r][c], cr.src[gi * cr.src_ld + gj], b);
       }
   }
   if (I0 + S <= n && J0 + S <= n) {
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      T *row = d + (I0 + ty + G * r) * ld + J0 + 4 * tx;
+      T *row = cr.dst + (I0 + ty + G * r) * cr.dst_ld + J0 + 4 * tx;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         T v[4];
@@ -521,7 +534,7 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int64_t gi = I0 + ty + G * r, gj = J0 + (c / 4) * (S / 2) + 4 * tx + (c % 4);
-        if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(acc[r][c]) : acc[r][c];
+        if (gi < n && gj < n) cr.dst[gi * cr.dst_ld + gj] = last ? Arith<T>::finish(acc[r][c]) : acc[r][c];
       }
   }
   if (MODE == 1 && bp && row_panel) {
@@ -564,8 +577,8 @@ __device__ __forceinline__ float2 add2f(float2 a, float2 b) { return __fadd2_rn(
 template <int S, bool REVERSE, bool FULL, bool VIA = false>
 __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     fw_phase3_f32x2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBp,
-                    float *__restrict__ d, int64_t n, int64_t ld, int b, const TileSet ts,
-                    int16_t *__restrict__ via, int64_t via_ld, int *err) {
+                    const CRoute<float> cr, int64_t n, int b, const TileSet ts, int16_t *__restrict__ via,
+                    int64_t via_ld, int *err) {
   using P = P3Tma<S>;
   constexpr int G = P::G;
   constexpr int KS = P::KS;
@@ -604,8 +617,9 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
   // here and again after the main loop from copies the compiler cannot see
   // through, so that no address is kept live across the loop.
   float acc[8][8];
-  uint64_t cbase = reinterpret_cast<uint64_t>(d + ((int64_t)It * S + ty) * ld + (int64_t)Jt * S + 2 * tx);
-  const int64_t rstride = (int64_t)G * ld * (int64_t)sizeof(float);
+  uint64_t cbase =
+      reinterpret_cast<uint64_t>(cr.src + ((int64_t)It * S + ty) * cr.src_ld + (int64_t)Jt * S + 2 * tx);
+  int64_t rstride = (int64_t)G * cr.src_ld * (int64_t)sizeof(float);
   int rows_left = 0, cols_left = 0;  // (masked form) rows/cols of the tile inside the matrix, from this thread
   if (!FULL) {
     rows_left = (int)(n - ((int64_t)It * S + ty));
@@ -677,7 +691,8 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
 
   int It2 = It, Jt2 = Jt, ty2 = ty, tx2 = tx;
   asm volatile("" : "+r"(It2), "+r"(Jt2), "+r"(ty2), "+r"(tx2));
-  cbase = reinterpret_cast<uint64_t>(d + ((int64_t)It2 * S + ty2) * ld + (int64_t)Jt2 * S + 2 * tx2);
+  cbase = reinterpret_cast<uint64_t>(cr.dst + ((int64_t)It2 * S + ty2) * cr.dst_ld + (int64_t)Jt2 * S + 2 * tx2);
+  rstride = (int64_t)G * cr.dst_ld * (int64_t)sizeof(float);
   if (!FULL) {
     rows_left = (int)(n - ((int64_t)It2 * S + ty2));
     cols_left = (int)(n - ((int64_t)Jt2 * S + 2 * tx2));
@@ -690,7 +705,7 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int64_t gi = (int64_t)It2 * S + ty2 + G * r, gj = (int64_t)Jt2 * S + 2 * tx2 + 2 * G * m + e;
-          if (gi < n && gj < n) note_via(via, via_ld, gi, gj, acc[r][2 * m + e], d[gi * ld + gj], b);
+          if (gi < n && gj < n) note_via(via, via_ld, gi, gj, acc[r][2 * m + e], cr.src[gi * cr.src_ld + gj], b);
         }
   }
 #pragma unroll
