@@ -458,7 +458,9 @@ def run_reference(a):
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if a.dtype == "f32" else "int64", "data": "synthetic",
-        "config": {"workload": _workload_name(a.dtype, n_sample), "sample_n": n_sample},
+        "config": {"workload": _workload_name(a.dtype, a.n), "sample_n": n_sample,
+                   "sample": f"each step solves the same generator at n={n_sample} (the oracle's O(n^3) loop "
+                             "at the full size would take hours); relaxations/s = n^3/t"},
         "cpu_baseline": {"value": value, "unit": "relaxations/s", "cores": 1, "kind": "oracle",
                          "sample": f"Fig. 1 triple loop, single thread, n={n_sample} per step"},
         "e2e": {"value": value, "unit": "relaxations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
