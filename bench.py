@@ -471,8 +471,10 @@ def run_reference(a):
 def _launches_per_solve(n, S, R, lookahead, dtype):
     """Kernel launches of one solve with n a multiple of S (the benchmark
     sizes): phase 1 and phase 2 per stage, phase 3 per stage, split into cross
-    + rest with the lookahead for every stage but the last."""
-    assert n % S == 0, "launch count derived for whole tiles only"
+    + rest with the lookahead for every stage but the last.  None for a ragged
+    n (edge-tile launches not counted here)."""
+    if n % S:
+        return None
     if R == 1:
         return 1
     return 2 * R + R + (R - 1 if lookahead else 0)
@@ -627,7 +629,8 @@ def run_ours(a):
                      "phase3_ms_mean": p3_mean_s * 1e3, "phase3_relax_per_launch": p3_relax_mean,
                      "schedule": "lookahead" if cfg.lookahead else "plain",
                      "phase1_ms_mean": statistics.mean(p1_ms), "phase2_ms_mean": statistics.mean(p2_ms)},
-        "gpu_launches": a.steps * _launches_per_solve(n, S, R, cfg.lookahead, a.dtype),
+        "gpu_launches": (lambda k: None if k is None else a.steps * k)(
+            _launches_per_solve(n, S, R, cfg.lookahead, a.dtype)),
         "clocks": clocks,
         "e2e": e2e,
         "paper_context": {"seconds_n16384_fp32_tesla_c1060": PAPER_SECONDS_N16384,
