@@ -141,6 +141,27 @@ def test_paths_lookahead_plain_and_graph_replay_agree():
     assert np.array_equal(d0, d1) and np.array_equal(v0, v1)
 
 
+def test_paths_tiny_graphs():
+    # n = 1 and 2 (one stage, phase 1 only) and a 2-cycle with an improvement
+    for w in (np.array([[0]], np.int32), np.array([[0, 5], [inputs.INF_I32, 0]], np.int32),
+              np.array([[0, 10, 1], [1, 0, inputs.INF_I32], [inputs.INF_I32, 2, 0]], np.int32)):
+        d, via = _solve_paths(w)
+        np.testing.assert_array_equal(d, oracle.fw_int32_conv(w))
+        n = w.shape[0]
+        for i in range(n):
+            for j in range(n):
+                p = binding.path(d, via, i, j, binding.query_config(n, binding.APSP_I32).kblock)
+                if i == j:
+                    assert p == [i]
+                elif d[i, j] >= (1 << 28):
+                    assert p == []
+                else:
+                    _check_path("i32", w, d, p, i, j)
+    # the 3-vertex case: 0 -> 1 improves from 10 to 3 through 2 (stage 0)
+    d, via = _solve_paths(np.array([[0, 10, 1], [1, 0, inputs.INF_I32], [inputs.INF_I32, 2, 0]], np.int32))
+    assert d[0, 1] == 3 and via[0, 1] == 0 and via[0, 2] == -1
+
+
 def test_paths_bad_arguments():
     t = torch.zeros((8, 8), dtype=torch.int32, device="cuda")
     v = torch.zeros((8, 8), dtype=torch.int16, device="cuda")
