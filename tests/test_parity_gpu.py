@@ -156,6 +156,39 @@ def test_capture_into_user_graph():
     np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
 
 
+# ------------------------------------------------ closed forms on the GPU ---
+
+@pytest.mark.parametrize("n", [300, 1100])
+def test_closed_forms_on_gpu(n):
+    # results the definition fixes without any oracle: a complete graph with
+    # all weights c (d_ij = c), the directed cycle 0 -> 1 -> ... -> n-1 -> 0
+    # with unit weights (d_ij = (j - i) mod n) and the chain with weights
+    # w_i,i+1 = i + 1 (d_ij = prefix-sum difference for i < j, unreachable
+    # backwards), in int32, fp32 (integer-valued: exact) and int16
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    cases = []
+    w = np.full((n, n), 7, np.int32)
+    np.fill_diagonal(w, 0)
+    cases.append((w, np.where(i == j, 0, 7)))
+    w = np.full((n, n), inputs.INF_I32, np.int32)
+    np.fill_diagonal(w, 0)
+    w[np.arange(n), (np.arange(n) + 1) % n] = 1
+    cases.append((w, (j - i) % n))
+    w = np.full((n, n), inputs.INF_I32, np.int32)
+    np.fill_diagonal(w, 0)
+    w[np.arange(n - 1), np.arange(1, n)] = np.arange(1, n)
+    pre = np.concatenate([[0], np.cumsum(np.arange(1, n))])
+    cases.append((w, np.where(j >= i, pre[j] - pre[i], inputs.INF_I32)))
+    for w, exp in cases:
+        np.testing.assert_array_equal(gpu_solve(w), exp)
+        f = np.where(w >= inputs.INF_I32, np.inf, w).astype(np.float32)
+        ef = np.where(exp >= inputs.INF_I32, np.inf, exp).astype(np.float32)
+        np.testing.assert_array_equal(gpu_solve(f), ef)  # integer sums < 2^24: exact
+        if exp[exp < inputs.INF_I32].max() < inputs.INF_I16:
+            np.testing.assert_array_equal(gpu_solve(inputs.to_int16(w)),
+                                          np.where(exp >= inputs.INF_I32, inputs.INF_I16, exp).astype(np.int16))
+
+
 # --------------------------------------------------- lookahead schedule ---
 
 def _graph(dt, n, seed):
