@@ -70,7 +70,7 @@ typedef enum apsp_status {
     APSP_OK = 0,
     APSP_EINVAL = 1,      /* bad argument (null pointer, n < 0, ld < n, ...)  */
     APSP_ENOMEM = 2,      /* an allocation failed                              */
-    APSP_EUNSUPPORTED = 3,/* valid request this build cannot serve             */
+    APSP_EUNSUPPORTED = 3,/* valid request the library cannot serve           */
     APSP_ECUDA = 4,       /* a CUDA runtime call failed                        */
     APSP_ETIMEOUT = 5,    /* a bounded device-side wait gave up                */
     APSP_EBUSY = 6,       /* resource in use (serving: no slot / memory)       */
