@@ -87,6 +87,13 @@ int run_i32(const RunArgs &a);
 int run_f32(const RunArgs &a);
 int run_i16(const RunArgs &a);
 
+// Checks and conversions around a solve (checks.cu); each returns an
+// apsp_status.  validate_input and check_negcycle synchronize the stream.
+int validate_input(const void *dist, int64_t n, int64_t ld, int dtype, cudaStream_t st, bool narrow);
+int check_negcycle(void *dist, int64_t n, int64_t ld, int dtype, cudaStream_t st, int *neg);
+int narrow_to_i16(const int32_t *src, int64_t n, int64_t ld, int16_t *dst, int64_t ld16, cudaStream_t st);
+int widen_from_i16(const int16_t *src, int64_t ld16, int64_t n, int32_t *dst, int64_t ld, cudaStream_t st);
+
 // Tile side the C ABI picks for (n, dtype) when none is requested.
 int default_kblock(int64_t n, int dtype);
 // Device address of the device error word of the current device (set-up once
