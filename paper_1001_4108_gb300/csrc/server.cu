@@ -127,10 +127,20 @@ void fail(Request *r, int rc) {
 }
 
 // Launches admitted requests (called without s->mu).
+// Integer requests below this count in one admission round are solved one
+// by one on all SMs rather than one CTA each: the batched kernel pays off
+// when it has many graphs to spread over the SMs.  (fp32 requests always take
+// the batched kernel when small, so that their rounding never depends on the
+// load; integer results are exact either way.)
+constexpr int kMinIntBatch = 8;
+
 void launch_admitted(Server *s, std::vector<Request *> &adm) {
+  int small_int = 0;
+  for (Request *r : adm)
+    if (r->n <= kBatchCtaMaxN && r->dtype != APSP_F32) ++small_int;
   std::vector<Request *> small;
   for (Request *r : adm) {
-    if (r->n <= kBatchCtaMaxN) {
+    if (r->n <= kBatchCtaMaxN && (r->dtype == APSP_F32 || small_int >= kMinIntBatch)) {
       small.push_back(r);
       continue;
     }
