@@ -611,6 +611,8 @@ def run_ours(a):
         "dtype": a.dtype, "data": "synthetic",
         "config": {"workload": _workload_name(a.dtype, n), "n": n, "kblock": cfg.kblock, "rounds": R,
                    "l2": "inputs larger than L2 (matrix %.2f GiB)" % (n * n * es / 2 ** 30),
+                   "input_restore": "the solve is in place: each timed step first copies the input back "
+                                    "on the device (one device-to-device copy, inside the timed region)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu",
                      "kernel": {"f32": "fw_phase3_f32x2", "i32": "fw_tile_tma<int,S,0>",
