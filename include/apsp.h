@@ -123,7 +123,7 @@ typedef struct apsp_options {
     void **events;
     int64_t n_events;
     /* Optional device workspace of apsp_workspace_bytes(n, dtype, kblock)
-       bytes (at least one panel buffer, half of that from 8 stages on: then
+       bytes (at least one panel buffer, half of that from 3 stages on: then
        the plain schedule runs), 256-byte aligned, owned by the caller and used
        only between the enqueue and the completion of this call's work on its
        stream; smaller: APSP_EINVAL.
@@ -141,7 +141,7 @@ typedef struct apsp_config {
     int32_t phase3_threads;  /* threads per phase-3 CTA                             */
     int64_t phase3_relax_per_round; /* relaxations phase 3 performs in a full round */
     int32_t lookahead;       /* 1 if a call without flags uses the lookahead schedule
-                                (stages >= 8, TMA-staged kernels, library workspace) */
+                                (stages >= 3, TMA-staged kernels, library workspace) */
     int32_t reserved;
 } apsp_config;
 
@@ -231,7 +231,7 @@ APSP_API int apsp_path(const void *dist, const int16_t *via, int64_t n, int64_t 
  * solves a copy of the current pivot column panel with every entry duplicated
  * into both halves of a 32-bit word; both are s * ceil(n/s) * s * 4 bytes
  * (8 MiB at n = 16384, s = 128), written by phase 2 and read by phase 3.
- * From 8 stages on, two such buffers (the lookahead schedule writes the next
+ * From 3 stages on, two such buffers (the lookahead schedule writes the next
  * stage's copy while phase 3 reads the current one); a workspace holding one
  * buffer runs the plain schedule.  Without a workspace the same results come
  * from slower phase-3 kernels.

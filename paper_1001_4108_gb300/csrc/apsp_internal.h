@@ -43,7 +43,7 @@ struct RunArgs {
 // Events a traced solve records per stage (apsp_options.events).
 constexpr int kEventsPerStage = 5;
 // Smallest tile-grid side R for which the lookahead schedule is used.
-constexpr int kLookaheadMinRounds = 8;
+constexpr int kLookaheadMinRounds = 3;
 
 // Workspace bytes of the packed int16x2 phase 3 (replicated column panel:
 // n_p rows x s words).
