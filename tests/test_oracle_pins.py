@@ -59,6 +59,10 @@ def test_golden_hand_derived(path):
         wf = np.where(w == INF, np.inf, w.astype(np.float64))
         ef = np.where(exp == INF, np.inf, exp.astype(np.float64))
         np.testing.assert_array_equal(oracle.fw_f64(wf), ef)
+        # and the brute-force enumeration of simple paths
+        bd, bunr = _brute_as_arrays(oracle.brute_force_paths(w.astype(np.int64), w == INF))
+        np.testing.assert_array_equal(bunr, exp == INF)
+        np.testing.assert_array_equal(bd[~bunr], exp[~bunr])
     else:
         w = np.array([[np.inf if t == "inf" else float(t) for t in r] for r in rin])
         exp = np.array([[np.inf if t == "inf" else float(t) for t in r] for r in rout])
