@@ -147,6 +147,22 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
 }
 
 // Index of a pivot-excluding tile: tiles b (the pivot block) is skipped.
+// Programmatic dependent launch.  The stage kernels are launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization, so one may be scheduled
+// while the kernel before it on the stream is still finishing (its launch and
+// prologue overlap that kernel's tail).  Each calls this before its first
+// access to the matrix or the panel workspace: it returns once the prior grid
+// has completed and its writes are visible.  Without that attribute it
+// returns at once.  APSP_PDL=0 builds both sides without it.
+#ifndef APSP_PDL
+#define APSP_PDL 1
+#endif
+__device__ __forceinline__ void wait_prior_grid() {
+#if APSP_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
 __device__ __forceinline__ int skip_pivot(int t, int b) { return t < b ? t : t + 1; }
 
 }  // namespace apsp

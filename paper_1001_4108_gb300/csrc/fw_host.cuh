@@ -105,8 +105,9 @@ struct Kernels {
   }
 };
 
-// Launches `k` on `st`; prio != 0 sets the launch's scheduling priority
-// (recorded in the node when the stream is being captured).
+// Launches `k` on `st` as a programmatic dependent launch (see
+// wait_prior_grid); prio != 0 sets the launch's scheduling priority (both
+// are recorded in the node when the stream is being captured).
 template <typename... KP, typename... Args>
 static cudaError_t launch(void (*k)(KP...), dim3 grid, int threads, size_t smem, cudaStream_t st, int prio,
                           Args... args) {
@@ -115,13 +116,21 @@ static cudaError_t launch(void (*k)(KP...), dim3 grid, int threads, size_t smem,
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
+  unsigned na = 0;
+#if APSP_PDL
+  // every kernel launched here starts with wait_prior_grid()
+  at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[na].val.programmaticStreamSerializationAllowed = 1;
+  ++na;
+#endif
   if (prio != 0) {
-    at[0].id = cudaLaunchAttributePriority;
-    at[0].val.priority = prio;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
+    at[na].id = cudaLaunchAttributePriority;
+    at[na].val.priority = prio;
+    ++na;
   }
+  cfg.attrs = na ? at : nullptr;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 

@@ -66,6 +66,7 @@ __device__ __forceinline__ void phase1_body(T *__restrict__ d, int64_t n, int64_
   const int tx = threadIdx.x % QC, ty = threadIdx.x / QC;
   const int64_t base = (int64_t)b * S;
   C x[MR][MC];
+  wait_prior_grid();
 #pragma unroll
   for (int a = 0; a < MR; ++a)
 #pragma unroll
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(NT) fw_phase2(T *__restrict__ d, int64_t n, in
   const int64_t pb = (int64_t)b * S;
   const int64_t r0 = row_panel ? pb : (int64_t)other * S;
   const int64_t c0 = row_panel ? (int64_t)other * S : pb;
+  wait_prior_grid();
 
 #pragma unroll
   for (int r = 0; r < E; ++r) {
@@ -234,6 +236,7 @@ __global__ void __launch_bounds__(256) fw_phase3_generic(T *__restrict__ d, int6
   const int64_t I0 = (int64_t)skip_pivot(blockIdx.y, b) * S;
   const int64_t J0 = (int64_t)skip_pivot(blockIdx.x, b) * S;
   const int64_t K0 = (int64_t)b * S;
+  wait_prior_grid();
 
   for (int e = threadIdx.x; e < S * S; e += 256) {
     const int r = e / S, c = e % S;
@@ -403,6 +406,7 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     tile_ij[1] = Jt;
   }
   __syncthreads();
+  wait_prior_grid();
   if (tid == 0) {
 #pragma unroll
     for (int s = 0; s < P::STAGES && s < P::NSL; ++s) {
@@ -604,6 +608,7 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     fence_mbar_init();
   }
   __syncthreads();
+  wait_prior_grid();
   if (tid == 0) {
 #pragma unroll
     for (int s = 0; s < P::STAGES && s < P::NSL; ++s) {
@@ -812,6 +817,7 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
     tile_ij[1] = Jt;
   }
   __syncthreads();
+  wait_prior_grid();
   if (DEFER_C && tid == 0) {
     mbar_arrive_expect_tx(cbar, P::C_BYTES);
     tma_load_2d(Cs, &tmC, cbar, Jt * S, It * S);
