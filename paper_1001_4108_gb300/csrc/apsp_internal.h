@@ -45,6 +45,22 @@ constexpr int kEventsPerStage = 5;
 // Smallest tile-grid side R for which the lookahead schedule is used.
 constexpr int kLookaheadMinRounds = 3;
 
+// Largest R for which the s = 64 panel and cross launches are cut into strips
+// (fw_strip).  While the bulk launch of a stage ((R-1)^2 tiles) fills only a
+// wave or two of the GPU, the stage waits on the panel/cross chain, and four
+// times as many CTAs per launch shorten it; beyond, the bulk launch bounds the
+// stage and the strips only take SM time from it.  Solve times with strips
+// against without, measured on GB300:
+//   R      24    32    40    48    56    64
+//   fp32  -29%  -23%  -13%   -2%   +4%   +8%
+//   int32 -12%  -18%   +8%  +11%   +6%   +5%
+// APSP_STRIP_MAX_ROUNDS (a build define) sets both limits, for such sweeps.
+#ifdef APSP_STRIP_MAX_ROUNDS
+constexpr int kStripMaxRoundsF32 = APSP_STRIP_MAX_ROUNDS, kStripMaxRoundsI32 = APSP_STRIP_MAX_ROUNDS;
+#else
+constexpr int kStripMaxRoundsF32 = 48, kStripMaxRoundsI32 = 32;
+#endif
+
 // Workspace bytes of the packed int16x2 phase 3 (replicated column panel:
 // n_p rows x s words).
 inline size_t replicated_panel_bytes(int64_t n, int S) {

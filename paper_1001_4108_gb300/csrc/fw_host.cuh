@@ -251,6 +251,7 @@ static int run_rounds(const RunArgs &a) {
   const bool lookahead = p3_tma && a.side && !(a.flags & APSP_FLAG_NO_LOOKAHEAD) && R >= kLookaheadMinRounds &&
                          (!needs_panel || nbuf == 2);
   auto buf_of = [&](int b) { return lookahead ? (b & 1) : 0; };
+  const bool strips = S == 64 && R <= (std::is_same<T, float>::value ? kStripMaxRoundsF32 : kStripMaxRoundsI32);
 
   auto ev = [&](int64_t idx, cudaStream_t s) -> bool {
     if (!a.events || idx >= a.n_events) return true;
@@ -276,6 +277,12 @@ static int run_rounds(const RunArgs &a) {
                       a.via_ld, a.err);
     }
     T *bpb = (use_packed && full_k(b)) ? bp[buf_of(b)] : nullptr;
+    if constexpr (HAS_TMA && S == 64 && !std::is_same<T, int16_t>::value) {
+      // four strips per panel tile while the stage is latency bound
+      if (use_tma && full_k(b) && strips)
+        return launch(fw_strip<T, S, 1, VIA>, dim3(8 * (R - 1)), 64, 0, s, prio, CRoute<T>{d, ld, d, ld},
+                      (const T *)d, n, ld, b, R, TileSet{}, last, reverse, bpb, 2 * np, a.via, a.via_ld);
+    }
     if constexpr (HAS_TMA) {
       if (use_tma && full_k(b))
         return launch(fw_tile_tma<T, S, 1, VIA>, g, P3Tma<S>::TPB, P3Tma<S>::SMEM, s, prio, mA, mB,
@@ -299,6 +306,16 @@ static int run_rounds(const RunArgs &a) {
       cr.dst_ld = a.last_dst_ld;
     }
     if (full_k(b)) {
+      if constexpr (HAS_TMA && S == 64 && !std::is_same<T, int16_t>::value) {
+        // the cross tiles of the lookahead schedule: as few as the panel
+        // tiles and on the critical path, so cut into strips as well
+        if (kind == kTilesCross && use_tma && strips) {
+          const TileSet ts = make_tileset(kind, kPartAny, b, R, ragged);
+          if (ts.total() == 0) return cudaSuccess;
+          return launch(fw_strip<T, S, 0, VIA>, dim3(4 * ts.total()), 64, 0, s, prio, cr, (const T *)d, n, ld, b,
+                        R, ts, last, reverse, (T *)nullptr, (int64_t)0, a.via, a.via_ld);
+        }
+      }
       if constexpr (std::is_same<T, int16_t>::value) {
         if (use_s16) {
           const TileSet ts = make_tileset(kind, kPartAny, b, R, ragged);

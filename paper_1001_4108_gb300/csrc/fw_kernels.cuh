@@ -728,6 +728,172 @@ __global__ void __launch_bounds__(P3Tma<S>::TPB, P3Tma<S>::MIN_BLOCKS)
     }
 }
 
+// ------------------------------------------- strips (latency-bound launches)
+// With s = 64 the panel launch of a stage has 2(R-1) tiles and the cross
+// launch of the lookahead schedule about as many; for small n that is fewer
+// tiles than SMs, and each runs as one 64-thread CTA on the stage's critical
+// path.  Here every tile is cut into four strips, one CTA each, so that four
+// times as many SMs share the work: 64 x 16 column strips, and 16 x 64 row
+// strips for the column-panel tiles (I, b).  The cut follows what each
+// output reads:
+//   row panel (b, J)     x_ij <- min(x_ij, min_k D_ik + x_kj): column j only;
+//   column panel (I, b)  x_ij <- min(x_ij, min_k x_ik + D_kj): row i only;
+//   other tiles          the two panels only;
+// so no strip reads what another strip of the launch writes.  D is closed
+// with a zero diagonal, so taking x_kj (x_ik) from before the update gives
+// the closure of the singly dependent tile: for integers the values of the
+// sequential k loop, and for fp32 those of the TMA kernels (every candidate is
+// one rounded sum and min is exact), so the result does not depend on which
+// kernel ran.  Needs a full k-block and 16-byte aligned rows (ld % 4 == 0),
+// as the TMA kernels do.
+//
+// Thread (tr, tc) of a RS x CS strip owns rows 4tr..4tr+3 and columns
+// 4tc..4tc+3; per k it reads four A values (shared memory keeps A transposed,
+// AT[k][r]) and four B values, each as one 128-bit load.
+template <typename T>
+struct Vec4;
+template <> struct Vec4<float> { using V = float4; };
+template <> struct Vec4<int32_t> { using V = int4; };
+
+// Elements j..j+3 of a row (j % 4 == 0), "infinity" from column n on; columns
+// n..ld-1 are not read.
+template <typename T>
+__device__ __forceinline__ typename Vec4<T>::V load_row4(const T *row, int64_t j, int64_t n) {
+  using V = typename Vec4<T>::V;
+  const T inf = Arith<T>::inf();
+  if (j + 4 <= n) return *reinterpret_cast<const V *>(row + j);
+  return V{j < n ? row[j] : inf, j + 1 < n ? row[j + 1] : inf, j + 2 < n ? row[j + 2] : inf, inf};
+}
+
+template <typename T, int S, int RS, int CS, bool VIA>
+__device__ __forceinline__ void strip_body(const CRoute<T> &cr, const T *__restrict__ d, int64_t n, int64_t ld, int b,
+                                           int64_t I0, int64_t J0, int last, int reverse, T *__restrict__ bp,
+                                           int64_t bp_ld, int16_t *__restrict__ via, int64_t via_ld, T *sm) {
+  using V = typename Vec4<T>::V;
+  T *AT = sm;            // [S][RS]
+  T *Bs = sm + S * RS;   // [S][CS]
+  constexpr int TC = CS / 4;
+  static_assert((RS / 4) * TC == 64, "64 threads, 4 x 4 each");
+  const int tid = threadIdx.x;
+  const int tr = tid / TC, tc = tid % TC;
+  const int64_t K0 = (int64_t)b * S;
+  const T inf = Arith<T>::inf();
+
+  // All global loads are issued before the first shared-memory store, so
+  // that their latencies overlap.
+  // A (rows I0.., the k-block's columns) -> AT[k][r]: the thread index runs
+  // along r, so the transposing stores hit consecutive banks.
+  constexpr int NA = RS * (S / 4) / 64, NB = S * (CS / 4) / 64;
+  V av[NA], bv[NB];
+#pragma unroll
+  for (int u = 0; u < NA; ++u) {
+    const int e = tid + 64 * u, r = e % RS, c4 = e / RS;
+    av[u] = I0 + r < n ? *reinterpret_cast<const V *>(d + (I0 + r) * ld + K0 + 4 * c4) : V{inf, inf, inf, inf};
+  }
+  // B (the k-block's rows, columns J0..) -> Bs[k][c]
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int e = tid + 64 * u, k = e / (CS / 4), c4 = e % (CS / 4);
+    bv[u] = load_row4(d + (K0 + k) * ld, J0 + 4 * c4, n);
+  }
+  // C -> registers
+  const int64_t gi0 = I0 + 4 * tr, gj0 = J0 + 4 * tc;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const V v = gi0 + a < n ? load_row4(cr.src + (gi0 + a) * cr.src_ld, gj0, n) : V{inf, inf, inf, inf};
+    acc[a][0] = v.x; acc[a][1] = v.y; acc[a][2] = v.z; acc[a][3] = v.w;
+  }
+#pragma unroll
+  for (int u = 0; u < NA; ++u) {
+    const int e = tid + 64 * u, r = e % RS, c4 = e / RS;
+    AT[(4 * c4 + 0) * RS + r] = av[u].x;
+    AT[(4 * c4 + 1) * RS + r] = av[u].y;
+    AT[(4 * c4 + 2) * RS + r] = av[u].z;
+    AT[(4 * c4 + 3) * RS + r] = av[u].w;
+  }
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int e = tid + 64 * u, k = e / (CS / 4), c4 = e % (CS / 4);
+    *reinterpret_cast<V *>(Bs + k * CS + 4 * c4) = bv[u];
+  }
+  __syncthreads();
+#pragma unroll 8
+  for (int kk = 0; kk < S; ++kk) {
+    const int k = reverse ? S - 1 - kk : kk;
+    const V ak = *reinterpret_cast<const V *>(AT + k * RS + 4 * tr);
+    const V bk = *reinterpret_cast<const V *>(Bs + k * CS + 4 * tc);
+    const T ar[4] = {ak.x, ak.y, ak.z, ak.w};
+    const T br[4] = {bk.x, bk.y, bk.z, bk.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = Arith<T>::relax(acc[a][c], ar[a], br[c]);
+  }
+  // the row panel also goes to the k-pair interleaved workspace (padding
+  // columns included) for the packed fp32 phase 3
+  if (bp) {
+#pragma unroll
+    for (int a = 0; a < 4; a += 2)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = 4 * tr + a;  // k within the block
+        T *p = bp + (int64_t)(i >> 1) * bp_ld + 2 * (gj0 + c);
+        p[0] = acc[a][c];
+        p[1] = acc[a + 1][c];
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t gi = gi0 + a;
+    if (gi >= n) continue;
+    if (VIA) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (gj0 + c < n) note_via(via, via_ld, gi, gj0 + c, acc[a][c], cr.src[gi * cr.src_ld + gj0 + c], b);
+    }
+    T o[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[c] = last ? Arith<T>::finish(acc[a][c]) : acc[a][c];
+    if (gj0 + 4 <= n) {
+      *reinterpret_cast<V *>(cr.dst + gi * cr.dst_ld + gj0) = V{o[0], o[1], o[2], o[3]};
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (gj0 + c < n) cr.dst[gi * cr.dst_ld + gj0 + c] = o[c];
+    }
+  }
+}
+
+// MODE 0: the tiles of `ts` (phase 3, C read and written through cr);
+// MODE 1: the 2(R-1) panel tiles of stage b (phase 2, C in the matrix).
+// Four CTAs per tile; bp (MODE 1 only) receives the row panel.
+template <typename T, int S, int MODE, bool VIA = false>
+__global__ void __launch_bounds__(64) fw_strip(const CRoute<T> cr, const T *__restrict__ d, int64_t n, int64_t ld,
+                                               int b, int R, const TileSet ts, int last, int reverse,
+                                               T *__restrict__ bp, int64_t bp_ld, int16_t *__restrict__ via,
+                                               int64_t via_ld) {
+  static_assert(S == 64, "strips are cut from 64 x 64 tiles");
+  __shared__ __align__(16) T sm[S * (S + S / 4)];  // A and B of one strip
+  const int t = blockIdx.x / 4, q = blockIdx.x % 4;
+  int It, Jt;
+  if (MODE == 0) {
+    ts.tile(t, It, Jt);
+  } else {
+    const bool rp = t < R - 1;
+    It = rp ? b : skip_pivot(t - (R - 1), b);
+    Jt = rp ? skip_pivot(t, b) : b;
+  }
+  wait_prior_grid();
+  const int64_t I0 = (int64_t)It * S, J0 = (int64_t)Jt * S;
+  if (MODE == 1 && Jt == b)  // column panel: row strips
+    strip_body<T, S, S / 4, S, VIA>(cr, d, n, ld, b, I0 + q * (S / 4), J0, last, reverse, nullptr, 0, via, via_ld,
+                                    sm);
+  else
+    strip_body<T, S, S, S / 4, VIA>(cr, d, n, ld, b, I0, J0 + q * (S / 4), last, reverse,
+                                    MODE == 1 ? bp : nullptr, bp_ld, via, via_ld, sm);
+}
+
 // --------------------------------------- phases 2 and 3, packed int16x2
 // int16 matrices (weights >= 0, (n-1) Wmax < 16383): two adjacent columns
 // are relaxed per 32-bit lane with one DPX viaddmin.s16x2:

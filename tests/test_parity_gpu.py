@@ -498,6 +498,51 @@ def test_host_entry_point_pinned(dt, n, ld):
     assert np.array_equal(t.cpu().numpy()[:, :n], h.numpy()[:, :n])
 
 
+# ------------------------------------------ both sides of the strip limit ---
+
+@pytest.mark.parametrize("dt,n", [("f32", 3000), ("f32", 3072), ("f32", 3100), ("f32", 3136),
+                                  ("i32", 2000), ("i32", 2048), ("i32", 2050), ("i32", 2112)])
+def test_strip_limit_sizes(dt, n):
+    """s = 64 solves on either side of the round count up to which the panel
+    and cross launches run as strips (fp32: R <= 48, int32: R <= 32), whole
+    and ragged: sampled rows against Dijkstra and the Bellman equation."""
+    cfg = binding.query_config(n, binding.APSP_F32 if dt == "f32" else binding.APSP_I32)
+    assert cfg.kblock == 64 and cfg.lookahead == 1
+    if dt == "f32":
+        w = inputs.dense_f32(n, seed=n)
+        g0 = np.random.default_rng(n)
+        w[g0.random((n, n)) < 0.9] = np.inf  # sparse: paths of several edges
+        np.fill_diagonal(w, 0)
+    else:
+        w = inputs.int_graph(n, 0.05, 1, 1000, seed=n)
+    t = torch.from_numpy(w).cuda()
+    binding.apsp_fw(t)
+    torch.cuda.synchronize()
+    d = t.cpu().numpy()
+    rows = inputs.rng(n).choice(n, size=24, replace=False)
+    if dt == "f32":
+        assert_fp32_close(d[rows], oracle.dijkstra_rows_f32(w, rows))
+    else:
+        np.testing.assert_array_equal(d[rows], oracle.dijkstra_rows_i32(w, rows))
+    # Bellman equation d_ij = min(w_ij, min_k w_ik + d_kj) on three rows
+    for i in rows[:3]:
+        if dt == "f32":
+            best = np.min(w[i].astype(np.float64)[:, None] + d.astype(np.float64), axis=0)
+            best = np.minimum(best, w[i])
+            best[i] = 0
+            fin = np.isfinite(best)
+            assert np.array_equal(np.isfinite(d[i]), fin)
+            assert np.all(np.abs(d[i][fin] - best[fin]) <= FP32_RTOL * np.abs(best[fin]) + 1e-30)
+        else:
+            wi = w[i].astype(np.int64)
+            dd = np.where(d < (1 << 28), d.astype(np.int64), 1 << 40)
+            best = np.min(np.where(wi[:, None] < inputs.INF_I32, wi[:, None] + dd, 1 << 40), axis=0)
+            best = np.minimum(best, np.where(wi < inputs.INF_I32, wi, 1 << 40))
+            best[i] = 0
+            best = np.where(best >= (1 << 28), inputs.INF_I32, best)
+            np.testing.assert_array_equal(d[i], best)
+
+
 # ------------------------------------------------------- full size, sampled ---
 
 @pytest.mark.parametrize("dt,n", [("f32", 16384), ("i32", 16384), ("f32", 32768)])
