@@ -105,7 +105,23 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def _parsed(self):
+        for t, line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                yield t, float(f[1]), float(f[2]), float(f[3]), f[5:9]
+            except ValueError:
+                continue
+
+    def window_mhz(self, t0: float, t1: float):
+        """Median SM clock of the samples that arrived between host times t0
+        and t1 (None if none did)."""
+        v = [sm for t, sm, _, _, _ in self._parsed() if t0 <= t <= t1]
+        return statistics.median(v) if v else None
 
     def stop(self):
         if self.proc is None:
@@ -119,17 +135,11 @@ class ClockSampler:
             self._t.join(timeout=2)
         sm, smax, reasons, power = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax = float(f[2])
-                power.append(float(f[3]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
+        for _, f_sm, f_smax, f_power, flags in self._parsed():
+            sm.append(f_sm)
+            smax = f_smax
+            power.append(f_power)
+            for nm, v in zip(names, flags):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
@@ -566,17 +576,27 @@ def run_ours(a):
         for _ in range(2):  # warm-up: allocates the device stage, captures the graph
             host.copy_(src)
             binding.apsp_fw_host(host)
-        ts = []
+        ts, windows = [], []
+        e2e_sampler = ClockSampler(local) if rank == 0 else None
+        if e2e_sampler:
+            e2e_sampler.start()
+            time.sleep(0.5)  # the first sample arrives after nvidia-smi starts
         for _ in range(a.e2e_steps):
             host.copy_(src)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             binding.apsp_fw_host(host)
-            ts.append(time.perf_counter() - t0)
+            t1 = time.perf_counter()
+            ts.append(t1 - t0)
+            windows.append((t0, t1))
+        e2e_clocks = None
+        if e2e_sampler:
+            e2e_clocks = e2e_sampler.stop()
+            e2e_clocks["sm_mhz_per_step"] = [e2e_sampler.window_mhz(t0, t1) for t0, t1 in windows]
         t_med = statistics.median(ts)
         e2e = {"value": world * relax_per_step / t_med, "unit": "relaxations/s",
                "h2d_bytes_per_step": n * n * es, "d2h_bytes_per_step": n * n * es,
-               "ms_per_step": t_med * 1e3, "ms_all_steps": [t * 1e3 for t in ts],
+               "ms_per_step": t_med * 1e3, "ms_all_steps": [t * 1e3 for t in ts], "clocks": e2e_clocks,
                "timing": "host clock around apsp_fw_host (pinned host matrix, H2D + solve + D2H), median of the steps"}
 
     if rank != 0:
