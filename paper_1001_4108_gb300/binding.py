@@ -44,7 +44,7 @@ class Config(ctypes.Structure):
     _fields_ = [("kblock", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("phase3_tma", ctypes.c_int32), ("phase3_threads", ctypes.c_int32),
                 ("phase3_relax_per_round", ctypes.c_int64), ("lookahead", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("strips", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):

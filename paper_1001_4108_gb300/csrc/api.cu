@@ -329,7 +329,7 @@ extern "C" int apsp_query_config(int64_t n, int dtype, int32_t kblock, apsp_conf
   const int64_t m = std::max<int64_t>(n - S, 0);
   cfg->phase3_relax_per_round = m * m * S;
   cfg->lookahead = cfg->rounds >= kLookaheadMinRounds ? 1 : 0;
-  cfg->reserved = 0;
+  cfg->strips = uses_strips(S, cfg->rounds, dtype == APSP_F32, dtype == APSP_I16) ? 1 : 0;
   return APSP_OK;
 }
 

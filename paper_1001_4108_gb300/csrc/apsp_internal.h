@@ -60,6 +60,11 @@ constexpr int kStripMaxRoundsF32 = APSP_STRIP_MAX_ROUNDS, kStripMaxRoundsI32 = A
 #else
 constexpr int kStripMaxRoundsF32 = 48, kStripMaxRoundsI32 = 32;
 #endif
+// Whether a solve with tile side S and R stages cuts its panel (and cross)
+// tiles into strips; int16 keeps its packed kernels.
+inline bool uses_strips(int S, int R, bool f32, bool i16) {
+  return S == 64 && !i16 && R >= 2 && R <= (f32 ? kStripMaxRoundsF32 : kStripMaxRoundsI32);
+}
 
 // Workspace bytes of the packed int16x2 phase 3 (replicated column panel:
 // n_p rows x s words).

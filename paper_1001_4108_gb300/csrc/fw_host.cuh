@@ -251,7 +251,7 @@ static int run_rounds(const RunArgs &a) {
   const bool lookahead = p3_tma && a.side && !(a.flags & APSP_FLAG_NO_LOOKAHEAD) && R >= kLookaheadMinRounds &&
                          (!needs_panel || nbuf == 2);
   auto buf_of = [&](int b) { return lookahead ? (b & 1) : 0; };
-  const bool strips = S == 64 && R <= (std::is_same<T, float>::value ? kStripMaxRoundsF32 : kStripMaxRoundsI32);
+  const bool strips = uses_strips(S, R, std::is_same<T, float>::value, std::is_same<T, int16_t>::value);
 
   auto ev = [&](int64_t idx, cudaStream_t s) -> bool {
     if (!a.events || idx >= a.n_events) return true;

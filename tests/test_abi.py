@@ -76,6 +76,15 @@ def test_query_config(L):
     assert L.apsp_query_config(10, 1, 100, ctypes.byref(cfg)) == binding.APSP_EINVAL
 
 
+def test_query_config_strips(L):
+    # strips: s = 64 panel/cross launches of up to 48 (fp32) / 32 (int32) stages
+    q = binding.query_config
+    assert [q(n, binding.APSP_F32).strips for n in (64, 65, 1024, 3072, 3073, 4096, 16384)] == [0, 1, 1, 1, 0, 0, 0]
+    assert [q(n, binding.APSP_I32).strips for n in (100, 2048, 2049, 4096)] == [1, 1, 0, 0]
+    assert q(1024, binding.APSP_I16).strips == 0
+    assert q(1024, binding.APSP_F32, 128).strips == 0
+
+
 def test_batched_bad_arguments(L):
     import ctypes as C
     P = (C.c_void_p * 2)(0x1000, 0)

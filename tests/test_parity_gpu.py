@@ -508,6 +508,7 @@ def test_strip_limit_sizes(dt, n):
     and ragged: sampled rows against Dijkstra and the Bellman equation."""
     cfg = binding.query_config(n, binding.APSP_F32 if dt == "f32" else binding.APSP_I32)
     assert cfg.kblock == 64 and cfg.lookahead == 1
+    assert cfg.strips == (cfg.rounds <= (48 if dt == "f32" else 32))
     if dt == "f32":
         w = inputs.dense_f32(n, seed=n)
         g0 = np.random.default_rng(n)
