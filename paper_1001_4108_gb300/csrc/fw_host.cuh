@@ -153,6 +153,11 @@ static cudaError_t launch(void (*k)(KP...), dim3 grid, int threads, size_t smem,
 // CTAs retire: the mostly serial phase 1 and the one-wave phase 2 no longer
 // leave the GPU idle between the phase-3 launches.  Every tile still sees
 // every stage in order, so results equal the plain schedule's bit for bit.
+//
+// Small matrices (uses_strips: s = 64, few stages): phase 2 and cross(b) have
+// fewer tiles than SMs and sit on the stage's critical path, so they run as
+// fw_strip launches, four CTAs per tile; the values are those of the TMA
+// kernels.
 template <typename T, int S, bool HAS_TMA, bool VIA>
 static int run_rounds(const RunArgs &a) {
   using K = Kernels<T, S>;
