@@ -264,9 +264,10 @@ APSP_API int apsp_fw_f32_noalloc(void *dist, int64_t n, int64_t ld, void *stream
 /*
  * Autotuner (the paper has none; in the spirit of the per-architecture code
  * generator it cites).  Times, on this GPU and for one element type:
- *   - the batched kernel shapes (tile side 32/64/128, 2x2 or 4x4 register
- *     block per thread) on synthetic batches for n buckets <= 32, 64, 128,
- *     256, 512, keeping the fastest shape per bucket;
+ *   - the batched kernel shapes (tile side / register block per thread:
+ *     32/2x2, 32/4x4, 64/4x4, 128/4x4) on synthetic batches for n buckets
+ *     <= 32, 64, 128, 256, 512, keeping the fastest shape per bucket, then a
+ *     few whole-batch assignments on a mixed batch;
  *   - the single-graph k-block depth (64 vs 128) at n = 1024 ... 6144,
  *     keeping the smallest n from which 128 stays faster.
  * The choices replace the built-in defaults for later calls in this process

@@ -97,7 +97,7 @@ def test_batched_padded_leading_dimension():
 def test_autotune_and_table_roundtrip(tmp_path):
     rep = binding.autotune(binding.APSP_I32)
     assert rep["dtype"] == "i32" and len(rep["batched"]) == 5 and len(rep["kblock"]) == 5
-    assert all(0 <= b["best"] < 4 for b in rep["batched"])
+    assert all(0 <= b["best"] < 4 and len(b["ms"]) == 4 for b in rep["batched"])
     path = str(tmp_path / "tuning.txt")
     binding.tuning_save(path)
     binding.tuning_load(path)
@@ -108,3 +108,38 @@ def test_autotune_and_table_roundtrip(tmp_path):
     torch.cuda.synchronize()
     for w, t in zip(ws, ts):
         np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_each_batched_shape(tmp_path, variant):
+    """Every kernel shape, forced through a tuning file for all n buckets,
+    gives the oracle's result (graphs of all buckets, ragged and whole tiles)."""
+    saved = str(tmp_path / "saved.txt")
+    binding.tuning_save(saved)
+    lines = open(saved).read().splitlines()
+    forced = [lines[0]]
+    for ln in lines[1:]:
+        f = ln.split()
+        i = f.index("batch_variants")
+        f[i + 1:i + 6] = [str(variant)] * 5
+        forced.append(" ".join(f))
+    path = str(tmp_path / "forced.txt")
+    open(path, "w").write("\n".join(forced) + "\n")
+    binding.tuning_load(path)
+    try:
+        g = inputs.rng(100 + variant)
+        ns = [1, 17, 32, 63, 64, 100, 128, 129, 250, 256, 300, 448, 512]
+        ws = [inputs.int_graph(n, 0.2, 0, 950, seed=int(g.integers(1 << 30)), potential_max=50) for n in ns]
+        ts = _to_gpu(ws)
+        binding.apsp_fw_batched(ts)
+        torch.cuda.synchronize()
+        for w, t in zip(ws, ts):
+            np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
+        fs = [inputs.dense_f32(n, seed=n) for n in (40, 200, 512)]
+        tf = _to_gpu(fs)
+        binding.apsp_fw_batched(tf)
+        torch.cuda.synchronize()
+        for w, t in zip(fs, tf):
+            assert np.allclose(t.cpu().numpy(), oracle.fw_f64(w), rtol=1e-5, atol=0)
+    finally:
+        binding.tuning_load(saved)
