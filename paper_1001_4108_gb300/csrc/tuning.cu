@@ -27,8 +27,10 @@ struct Table {
 // Defaults = choices measured on a GB300: shape (s 32, 4x4) up to n = 32,
 // (s 64, 4x4) up to 512 (on a mixed batch it beats using (s 128, 4x4) above
 // 256, which wins only when those graphs run alone); single-graph k-block 128
-// from n = 6144 (int16: 8192).
-Table g_tab = {{{1, 2, 2, 2, 2}, {1, 2, 2, 2, 2}, {1, 2, 2, 2, 2}}, {6144, 6144, 8192}, {0, 0, 0}};
+// from n = 4096 (int32), 4608 (fp32), 5120 (int16).  Solve times s = 128
+// over s = 64: int32 1.006 at 3584, 0.938 at 4096; fp32 1.054 at 4096,
+// 0.988 at 4608, 0.892 at 5120; int16 1.023 at 4096, 0.977 at 5120.
+Table g_tab = {{{1, 2, 2, 2, 2}, {1, 2, 2, 2, 2}, {1, 2, 2, 2, 2}}, {4096, 4608, 5120}, {0, 0, 0}};
 std::mutex g_tmu;
 
 int dtype_index(int dtype) { return dtype == APSP_F32 ? 1 : dtype == APSP_I16 ? 2 : 0; }

@@ -69,7 +69,11 @@ def test_query_config(L):
     c = binding.query_config(1000, binding.APSP_I32)
     assert c.kblock == 64 and c.rounds == 16
     assert binding.query_config(4096, binding.APSP_F32).kblock == 64
-    assert binding.query_config(6144, binding.APSP_F32).kblock == 128
+    assert binding.query_config(4608, binding.APSP_F32).kblock == 128
+    assert binding.query_config(4095, binding.APSP_I32).kblock == 64
+    assert binding.query_config(4096, binding.APSP_I32).kblock == 128
+    assert binding.query_config(5119, binding.APSP_I16).kblock == 64
+    assert binding.query_config(5120, binding.APSP_I16).kblock == 128
     c = binding.query_config(1000, binding.APSP_I16, 128)
     assert c.kblock == 128 and c.rounds == 8 and c.phase3_tma == 1
     cfg = binding.Config()
