@@ -142,9 +142,10 @@ typedef struct apsp_config {
     int64_t phase3_relax_per_round; /* relaxations phase 3 performs in a full round */
     int32_t lookahead;       /* 1 if a call without flags uses the lookahead schedule
                                 (stages >= 3, TMA-staged kernels, library workspace) */
-    int32_t strips;          /* 1 if the phase-2 launches (and the lookahead's cross
-                                launches) cut each 64 x 64 tile into four one-CTA
-                                strips: s = 64, fp32 up to 48 stages, int32 up to 32 */
+    int32_t strips;          /* 1 if a call without flags on 16-byte aligned rows cuts
+                                each 64 x 64 tile of its phase-2 launches (and of the
+                                lookahead's cross launches) into four one-CTA strips:
+                                s = 64, fp32 up to 48 stages, int32 up to 32 */
 } apsp_config;
 
 /* Status name, e.g. "APSP_EINVAL".  Never NULL. */
