@@ -135,8 +135,9 @@ void side_resources_locked(int dev, cudaStream_t stream, bool capturing, RunArgs
 }
 
 // ---------------------------------------------------------------- graphs
-// A solve is R * 3 launches.  Replaying them as one CUDA graph removes the
-// per-launch host cost, which dominates for small n.  A graph is captured the
+// A solve is 3 launches per stage (4 with the lookahead's split phase 3).
+// Replaying them as one CUDA graph removes the per-launch host cost, which
+// dominates for small n.  A graph is captured the
 // second time the same (matrix, n, ld, dtype, s, flags) is solved, so one-off
 // calls do not pay the instantiation.
 struct GraphKey {
