@@ -48,6 +48,9 @@ def _args():
     ap.add_argument("--batched", type=int, default=4096, help="graphs in the batched (c4) comparison; 0 = skip")
     ap.add_argument("--serving", type=int, default=240, help="requests in the serving (c5) sweep; 0 = skip")
     ap.add_argument("--paths", type=int, default=1, help="time the solve with path bookkeeping; 0 = skip")
+    ap.add_argument("--small", type=int, default=100, help="steps of the c1 / c3 timings; 0 = skip")
+    ap.add_argument("--other-dtype", type=int, default=1,
+                    help="also time the other 32-bit type (int32 beside fp32) at the same n; 0 = skip")
     return ap.parse_args()
 
 
@@ -198,12 +201,31 @@ def _measured_traffic(dtype: str, n: int, s: int, tiles: float):
     return e["bytes_per_launch"] / e["tiles_per_launch"] * tiles
 
 
+def _as_int32_convention(w):
+    """An int16 matrix (16383 = missing edge) re-encoded for the int32 oracle
+    entry points (2^29 = missing edge); int32 matrices are returned as is."""
+    import numpy as np
+    import oracle
+    if w.dtype == np.int16:
+        return np.where(w == oracle.ABSENT_I16, oracle.ABSENT_I32, w.astype(np.int32)).astype(np.int32)
+    return w
+
+
 def cpu_baseline(dtype: str, n_sample: int = 2048):
-    """The oracle as it stands (Fig. 1 triple loop, FP64 / int64, one thread)
-    on a bounded sample of the workload."""
+    """The oracle as it stands on a bounded sample of the workload: Fig. 1's
+    triple loop (FP64 for fp32 weights, int64 with infinity flags for
+    integers) once on every host core (the rows of each iteration k shared
+    among threads) and once on one thread (the paper's basic CPU run)."""
     import oracle
     w = _make_input(dtype, n_sample, seed=0)
     oracle.build()
+    kind = "FP64" if dtype == "f32" else "int64"
+    t0 = time.perf_counter()
+    if dtype == "f32":
+        _, used = oracle.fw_f64_mt(w)
+    else:
+        _, used = oracle.fw_int32_conv_mt(_as_int32_convention(w))
+    dt_mt = time.perf_counter() - t0
     t0 = time.perf_counter()
     if dtype == "f32":
         oracle.fw_f64(w)
@@ -211,11 +233,15 @@ def cpu_baseline(dtype: str, n_sample: int = 2048):
         oracle.fw_int16_conv(w)
     else:
         oracle.fw_int32_conv(w)
-    dt = time.perf_counter() - t0
-    return {"value": n_sample ** 3 / dt, "unit": "relaxations/s", "cores": 1, "kind": "oracle",
-            "sample": f"one Fig. 1 solve ({'FP64' if dtype == 'f32' else 'int64'}, single thread) of the same "
-                      f"generator at n={n_sample} ({dt:.2f} s); relaxations/s scale as n^3 / t",
-            "host_cpus": os.cpu_count()}
+    dt_1 = time.perf_counter() - t0
+    return {"value": n_sample ** 3 / dt_mt, "unit": "relaxations/s", "cores": used, "kind": "oracle",
+            "sample": f"one Fig. 1 solve ({kind}, {used} threads: rows of each k shared) of the same generator "
+                      f"at n={n_sample} ({dt_mt:.2f} s); relaxations/s scale as n^3 / t",
+            "host_cpus": os.cpu_count(),
+            "single_thread": {"value": n_sample ** 3 / dt_1, "unit": "relaxations/s", "cores": 1,
+                              "kind": "oracle",
+                              "sample": f"the same solve on one thread (the paper's basic CPU form), "
+                                        f"n={n_sample} ({dt_1:.2f} s)"}}
 
 
 def bench_paths(work, pristine, plain_ms: float, kblock: int, steps: int = 2, samples: int = 64):
@@ -448,19 +474,31 @@ def bench_serving(count: int = 240, seed: int = 6, rates=(0.25, 0.5, 1.0, 1.5), 
 
 
 def run_reference(a):
+    """The reference arm: this paper ships no code, so the arm is the oracle
+    (Fig. 1's triple loop, FP64 / int64, on every host core with the rows of
+    each iteration k shared among threads), one solve per step of the same
+    generator at a bounded sample size."""
     rank, world, _ = _dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
-    n_sample = 1024
+    n_sample = 2048
     w = _make_input(a.dtype, n_sample, seed=0)
-    f = {"f32": oracle.fw_f64, "i32": oracle.fw_int32_conv, "i16": oracle.fw_int16_conv}[a.dtype]
+    if a.dtype == "f32":
+        def f(x):
+            return oracle.fw_f64_mt(x)[1]
+    else:
+        w = _as_int32_convention(w)
+
+        def f(x):
+            return oracle.fw_int32_conv_mt(x)[1]
     for _ in range(a.warmup):
         f(w)
     t0 = time.perf_counter()
+    used = 1
     for _ in range(a.steps):
-        f(w)
+        used = f(w)
     dt = time.perf_counter() - t0
     value = a.steps * n_sample ** 3 / dt
     line = {
@@ -470,9 +508,10 @@ def run_reference(a):
         "dtype": "f64" if a.dtype == "f32" else "int64", "data": "synthetic",
         "config": {"workload": _workload_name(a.dtype, a.n), "sample_n": n_sample,
                    "sample": f"each step solves the same generator at n={n_sample} (the oracle's O(n^3) loop "
-                             "at the full size would take hours); relaxations/s = n^3/t"},
-        "cpu_baseline": {"value": value, "unit": "relaxations/s", "cores": 1, "kind": "oracle",
-                         "sample": f"Fig. 1 triple loop, single thread, n={n_sample} per step"},
+                             "at the full size would take minutes per step); relaxations/s = n^3/t"},
+        "cpu_baseline": {"value": value, "unit": "relaxations/s", "cores": used, "kind": "oracle",
+                         "sample": f"Fig. 1 triple loop on {used} threads (rows of each k shared), "
+                                   f"n={n_sample} per step"},
         "e2e": {"value": value, "unit": "relaxations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -490,32 +529,30 @@ def _launches_per_solve(n, S, R, lookahead, dtype):
     return 2 * R + R + (R - 1 if lookahead else 0)
 
 
-def run_ours(a):
-    import numpy as np
+def measure_single(a, dtype: str, n: int, steps: int, warmup: int, e2e_steps: int, seed: int,
+                   clock_gpu=None, world: int = 1):
+    """One solve per step of the `dtype` workload at size n: CUDA events on the
+    launching stream around `steps` solves (each restores the input first),
+    5 per-phase events per stage inside the timed region for the phase-3
+    launch's own rate, and host-timed solves through apsp_fw_host (pinned
+    host matrix, copies inside the timed region).  Returns the measurements
+    of this rank."""
     import torch
     import torch.distributed as dist
+    from paper_1001_4108_gb300 import binding
 
-    from paper_1001_4108_gb300 import binding, build
-
-    rank, world, local = _dist_env()
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    build.build()
-    L = binding.lib()
-    n = a.n
-    es = 2 if a.dtype == "i16" else 4
-    dcode = {"f32": binding.APSP_F32, "i32": binding.APSP_I32, "i16": binding.APSP_I16}[a.dtype]
+    es = 2 if dtype == "i16" else 4
+    dcode = {"f32": binding.APSP_F32, "i32": binding.APSP_I32, "i16": binding.APSP_I16}[dtype]
     cfg = binding.query_config(n, dcode, a.kblock)
     R = cfg.rounds
-    w = _make_input(a.dtype, n, seed=rank)
+    w = _make_input(dtype, n, seed=seed)
     pristine = torch.from_numpy(w).cuda()
     work = torch.empty_like(pristine)
     stream = torch.cuda.current_stream()
 
     E = binding.EVENTS_PER_STAGE
     nev = E * R
-    step_events = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(a.steps)]
+    step_events = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(steps)]
     for evs in step_events:  # torch creates the CUDA event on its first record
         for e in evs:
             e.record(stream)
@@ -524,12 +561,12 @@ def run_ours(a):
         work.copy_(pristine)
         binding.apsp_fw(work, kblock=a.kblock, events=events, flags=binding.FLAG_NO_GRAPH)
 
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     assert binding.device_error() == 0
 
-    sampler = ClockSampler(local) if rank == 0 else None
+    sampler = ClockSampler(clock_gpu) if clock_gpu is not None else None
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -539,7 +576,7 @@ def run_ours(a):
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for k in range(a.steps):
+    for k in range(steps):
         step(step_events[k])   # per-phase events recorded on the launching stream
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -566,22 +603,22 @@ def run_ours(a):
     assert binding.device_error() == 0
 
     relax_per_step = float(n) ** 3
-    value = job_value(a.steps * relax_per_step, world, total_ms * 1e-3)
+    value = job_value(steps * relax_per_step, world, total_ms * 1e-3)
 
     # e2e: the host entry point (pinned host matrix -> H2D -> solve -> D2H)
     e2e = None
-    if a.e2e_steps > 0:
+    if e2e_steps > 0:
         host = torch.from_numpy(w).pin_memory()
         src = host.clone()
         for _ in range(2):  # warm-up: allocates the device stage, captures the graph
             host.copy_(src)
             binding.apsp_fw_host(host)
         ts, windows = [], []
-        e2e_sampler = ClockSampler(local) if rank == 0 else None
+        e2e_sampler = ClockSampler(clock_gpu) if clock_gpu is not None else None
         if e2e_sampler:
             e2e_sampler.start()
             time.sleep(0.5)  # the first sample arrives after nvidia-smi starts
-        for _ in range(a.e2e_steps):
+        for _ in range(e2e_steps):
             host.copy_(src)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -598,6 +635,132 @@ def run_ours(a):
                "h2d_bytes_per_step": n * n * es, "d2h_bytes_per_step": n * n * es,
                "ms_per_step": t_med * 1e3, "ms_all_steps": [t * 1e3 for t in ts], "clocks": e2e_clocks,
                "timing": "host clock around apsp_fw_host (pinned host matrix, H2D + solve + D2H), median of the steps"}
+    return {"cfg": cfg, "value": value, "total_ms": total_ms, "p1_ms": p1_ms, "p2_ms": p2_ms, "p3_ms": p3_ms,
+            "p3_relax": p3_relax, "clocks": clocks, "e2e": e2e, "work": work, "pristine": pristine, "es": es}
+
+
+def roofline_block(dtype: str, n: int, m: dict, sms: int, peaks: dict, peak_kind: str, form_ceiling: float):
+    """ALU roofline of the phase-3 launch: relaxations of the launches with a
+    full k-block over their summed event durations, against the min-plus
+    peak.  Every candidate d_ik + d_kj needs one 32-bit minimum, and minima
+    run on the ALU pipe: 16 lanes per SM sub-partition, 64 per SM per clock.
+    int32 and fp32: 64 relaxations/clock/SM (a three-input min folds two
+    candidates but retires them at the same rate, measured: forms 4 and 5 of
+    apsp_ubench_minplus); int16x2: two relaxations per DPX lane,
+    128/clock/SM."""
+    S = m["cfg"].kblock
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    lanes = 128 if dtype == "i16" else 64
+    peak = sms * sm_max * 1e6 * lanes
+    p3_ms, p3_relax = m["p3_ms"], m["p3_relax"]
+    p3_mean_s = statistics.mean(p3_ms) * 1e-3 if p3_ms else float("nan")
+    achieved = sum(p3_relax) / (sum(p3_ms) * 1e-3) if p3_ms else float("nan")
+    p3_relax_mean = statistics.mean(p3_relax) if p3_relax else float("nan")
+    hbm_bytes = 2.0 * m["es"] * p3_relax_mean / S  # C tile read + write per phase-3 launch
+    return {"bound": "alu",
+            "kernel": {"f32": f"fw_phase3_f32x2<{S},...>", "i32": f"fw_tile_tma<int,{S},0>",
+                       "i16": f"fw_tile_s16x2<{S},0>"}[dtype],
+            "achieved": achieved, "peak": peak,
+            "unit": "relaxations/s", "frac": achieved / peak,
+            "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz ({peak_kind} max clock) x {lanes} relaxations "
+                          "per clock per SM (one 32-bit min per candidate on 64 ALU-pipe lanes; "
+                          "int16x2: 2 per DPX lane)",
+            "form_ceiling": form_ceiling, "frac_of_form_ceiling": achieved / form_ceiling,
+            "traffic": _measured_traffic(dtype, n, S, p3_relax_mean / S ** 3),
+            "traffic_source": "ncu dram__bytes_read+write of the same launch kind at n=8192, "
+                              "scaled by tile count",
+            "algorithmic_hbm_GBps": hbm_bytes / p3_mean_s / 1e9,
+            "hbm_peak_GBps": peaks.get("hbm_gbs"),
+            "phase3_ms_mean": p3_mean_s * 1e3, "phase3_relax_per_launch": p3_relax_mean,
+            "schedule": "lookahead" if m["cfg"].lookahead else "plain",
+            "phase1_ms_mean": statistics.mean(m["p1_ms"]), "phase2_ms_mean": statistics.mean(m["p2_ms"])}
+
+
+def bench_small_config(name: str, w, steps: int = 100, flush_mb: int = 256):
+    """A small workload (matrix smaller than L2): one solve per step through
+    apsp_fw (the library's graph replay), each step timed by its own pair of
+    CUDA events; between steps the input is restored and a buffer larger than
+    L2 is written (both outside the event pair).  Returns the median and mean
+    step time and relaxations/s of the mean."""
+    import torch
+    from paper_1001_4108_gb300 import binding
+    n = w.shape[0]
+    pristine = torch.from_numpy(w).cuda()
+    work = torch.empty_like(pristine)
+    flush = torch.empty(flush_mb << 18, dtype=torch.float32, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for _ in range(5):
+        work.copy_(pristine)
+        binding.apsp_fw(work)
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        work.copy_(pristine)
+        flush.fill_(1.0)
+        e0.record()
+        binding.apsp_fw(work)
+        e1.record()
+    torch.cuda.synchronize()
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    mean = statistics.mean(ms)
+    return {"workload": name, "n": n, "ms_per_step_mean": mean, "ms_per_step_median": statistics.median(ms),
+            "value": float(n) ** 3 / (mean * 1e-3), "unit": "relaxations/s", "steps": steps,
+            "l2": f"flushed between steps ({flush_mb} MiB write outside the timed events)",
+            "timing": "CUDA events around each apsp_fw call (graph replay), input restore outside"}, work
+
+
+def bench_small_configs(steps: int = 100):
+    """c1 (n = 1024 int32, p = 0.3) and c3 (n = 2048, p = 0.1, weights 1..7:
+    int16x2 beside int32), each checked bit for bit against the oracle (all
+    host cores) and, for c3, the two encodings against each other."""
+    import numpy as np
+    import oracle
+    from paper_1001_4108_gb300 import inputs
+    out = {}
+    w1 = inputs.c1(seed=0)
+    r1, d1 = bench_small_config("c1: n=1024, edge probability 0.3, int32 weights in [1,1000]", w1, steps)
+    r1["bit_exact_vs_oracle"] = bool(np.array_equal(d1.cpu().numpy(), oracle.fw_int32_conv_mt(w1)[0]))
+    out["c1"] = r1
+    w32, w16 = inputs.c3(seed=0)
+    r32, d32 = bench_small_config("c3 int32: n=2048, edge probability 0.1, weights in [1,7]", w32, steps)
+    r16, d16 = bench_small_config("c3 int16x2: the same graph in int16", w16, steps)
+    e32 = oracle.fw_int32_conv_mt(w32)[0]
+    d16h = d16.cpu().numpy()
+    r16["bit_exact_vs_oracle"] = bool(np.array_equal(d16h, inputs.to_int16(e32)))
+    r32["bit_exact_vs_oracle"] = bool(np.array_equal(d32.cpu().numpy(), e32))
+    r16["bit_exact_vs_int32"] = bool(np.array_equal(
+        np.where(d16h == inputs.INF_I16, inputs.INF_I32, d16h.astype(np.int32)), d32.cpu().numpy()))
+    out["c3"] = {"int32": r32, "int16x2": r16, "speedup_int16x2": r32["ms_per_step_mean"] / r16["ms_per_step_mean"]}
+    assert r1["bit_exact_vs_oracle"] and r32["bit_exact_vs_oracle"] and r16["bit_exact_vs_oracle"] \
+        and r16["bit_exact_vs_int32"], "small configs differ from the oracle"
+    return out
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1001_4108_gb300 import binding, build
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    binding.lib()
+    n = a.n
+    m = measure_single(a, a.dtype, n, a.steps, a.warmup, a.e2e_steps, seed=rank,
+                       clock_gpu=local if rank == 0 else None, world=world)
+    m.pop("work"), m.pop("pristine")
+    torch.cuda.empty_cache()
+    cfg, R, S = m["cfg"], m["cfg"].rounds, m["cfg"].kblock
+    # the other 32-bit type of the headline metric (fp32 / int32 at n = 16384)
+    other = {"f32": "i32", "i32": "f32"}.get(a.dtype) if a.other_dtype else None
+    m2 = None
+    if other:
+        m2 = measure_single(a, other, n, a.steps, a.warmup, a.e2e_steps, seed=rank,
+                            clock_gpu=local if rank == 0 else None, world=world)
+        m2.pop("work"), m2.pop("pristine")
+        torch.cuda.empty_cache()
 
     if rank != 0:
         if world > 1:
@@ -606,60 +769,50 @@ def run_ours(a):
 
     peaks, peak_kind = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # Min-plus ALU roofline.  Every candidate d_ik + d_kj needs one 32-bit
-    # minimum, and minima run on the ALU pipe: 16 lanes per SM sub-partition,
-    # 64 per SM per clock.  int32 and fp32: 64 relaxations/clock/SM (a
-    # three-input min folds two candidates but retires them at the same rate,
-    # measured: forms 4 and 5 of apsp_ubench_minplus); int16x2: two
-    # relaxations per DPX lane, 128/clock/SM.
-    lanes = 128 if a.dtype == "i16" else 64
-    peak = sms * sm_max * 1e6 * lanes
     # the same instruction form in isolation (phase-3 inner loop on shared-
     # memory operands, every SM): the sustained ceiling of the form
     sink = torch.empty(sms * 2 * 256, dtype=torch.int32, device="cuda")
-    form_ceiling = binding.ubench({"f32": 4, "i32": 0, "i16": 2}[a.dtype], 2000, sink)
-    p3_mean_s = statistics.mean(p3_ms) * 1e-3 if p3_ms else float("nan")
-    achieved = sum(p3_relax) / (sum(p3_ms) * 1e-3) if p3_ms else float("nan")
-    p3_relax_mean = statistics.mean(p3_relax) if p3_relax else float("nan")
-    hbm_bytes = 2.0 * es * p3_relax_mean / S  # C tile read + write per phase-3 launch
+    forms = {"f32": 4, "i32": 0, "i16": 2}
+    ceiling = {dt: binding.ubench(forms[dt], 2000, sink) for dt in {a.dtype, other} if dt}
+    total_ms = m["total_ms"]
     line = {
-        "metric": "relaxations/s (n^3/t)", "value": value, "unit": "relaxations/s",
+        "metric": "relaxations/s (n^3/t)", "value": m["value"], "unit": "relaxations/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
         "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": value / (float(a.n) ** 3 / PAPER_SECONDS_N16384) if a.n == 16384 and a.dtype == "f32" else None,
+        "vs_baseline": (m["value"] / (float(a.n) ** 3 / PAPER_SECONDS_N16384)
+                        if a.n == 16384 and a.dtype == "f32" else None),
         "dtype": a.dtype, "data": "synthetic",
-        "config": {"workload": _workload_name(a.dtype, n), "n": n, "kblock": cfg.kblock, "rounds": R,
-                   "l2": "inputs larger than L2 (matrix %.2f GiB)" % (n * n * es / 2 ** 30),
+        "config": {"workload": _workload_name(a.dtype, n), "n": n, "kblock": S, "rounds": R,
+                   "l2": "inputs larger than L2 (matrix %.2f GiB)" % (n * n * m["es"] / 2 ** 30),
                    "input_restore": "the solve is in place: each timed step first copies the input back "
                                     "on the device (one device-to-device copy, inside the timed region)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "alu",
-                     "kernel": {"f32": "fw_phase3_f32x2", "i32": "fw_tile_tma<int,S,0>",
-                                "i16": "fw_tile_s16x2<S,0>"}[a.dtype],
-                     "achieved": achieved, "peak": peak,
-                     "unit": "relaxations/s", "frac": achieved / peak,
-                     "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz ({peak_kind} max clock) x {lanes} relaxations "
-                                   "per clock per SM (one 32-bit min per candidate on 64 ALU-pipe lanes; "
-                                   "int16x2: 2 per DPX lane)",
-                     "form_ceiling": form_ceiling, "frac_of_form_ceiling": achieved / form_ceiling,
-                     "traffic": _measured_traffic(a.dtype, n, S, p3_relax_mean / S ** 3),
-                     "traffic_source": "ncu dram__bytes_read+write of the same launch kind at n=8192, "
-                                       "scaled by tile count",
-                     "algorithmic_hbm_GBps": hbm_bytes / p3_mean_s / 1e9,
-                     "hbm_peak_GBps": peaks.get("hbm_gbs"),
-                     "phase3_ms_mean": p3_mean_s * 1e3, "phase3_relax_per_launch": p3_relax_mean,
-                     "schedule": "lookahead" if cfg.lookahead else "plain",
-                     "phase1_ms_mean": statistics.mean(p1_ms), "phase2_ms_mean": statistics.mean(p2_ms)},
+        "roofline": roofline_block(a.dtype, n, m, sms, peaks, peak_kind, ceiling[a.dtype]),
         "gpu_launches": (lambda k: None if k is None else a.steps * k)(
             _launches_per_solve(n, S, R, cfg.lookahead, a.dtype)),
-        "clocks": clocks,
-        "e2e": e2e,
+        "clocks": m["clocks"],
+        "e2e": m["e2e"],
         "paper_context": {"seconds_n16384_fp32_tesla_c1060": PAPER_SECONDS_N16384,
                           "ours_seconds": total_ms / a.steps / 1e3},
     }
+    if m2 is not None:
+        c2 = m2["cfg"]
+        line[{"i32": "int32", "f32": "fp32"}[other]] = {
+            "workload": _workload_name(other, n), "value": m2["value"], "unit": "relaxations/s",
+            "ms_per_step": m2["total_ms"] / a.steps, "steps": a.steps, "warmup": a.warmup,
+            "kblock": c2.kblock, "rounds": c2.rounds,
+            "roofline": roofline_block(other, n, m2, sms, peaks, peak_kind, ceiling[other]),
+            "gpu_launches": (lambda k: None if k is None else a.steps * k)(
+                _launches_per_solve(n, c2.kblock, c2.rounds, c2.lookahead, other)),
+            "clocks": m2["clocks"], "e2e": m2["e2e"],
+            "timing": "as the main line: CUDA events on the launching stream, input restore inside"}
+    if a.small > 0:
+        line["small_configs"] = bench_small_configs(a.small)
     if a.paths > 0:
-        line["paths"] = bench_paths(work, pristine, total_ms / a.steps, S)
+        pristine = torch.from_numpy(_make_input(a.dtype, n, seed=rank)).cuda()
+        line["paths"] = bench_paths(torch.empty_like(pristine), pristine, total_ms / a.steps, S)
+        del pristine
+        torch.cuda.empty_cache()
     if a.batched > 0:
         line["batched"] = bench_batched(a.batched)
     if a.serving > 0:

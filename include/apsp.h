@@ -252,7 +252,11 @@ APSP_API int64_t apsp_workspace_bytes(int64_t n, int dtype, int32_t kblock);
  * The scratch the packed phase 3 needs (the interleaved row panel) lives in a
  * static device array of the library, 8 MiB, held by every GPU that loads the
  * library until the process exits.  Limit: n <= 16384; larger n returns
- * APSP_EUNSUPPORTED before any device work.  The first call on each device
+ * APSP_EUNSUPPORTED before any device work.  With dist 16-byte aligned, ld * 4
+ * a multiple of 16 and n above one tile, the solve always runs the packed
+ * kernels on the array (if they cannot run, the call returns
+ * APSP_EUNSUPPORTED before any device work); other layouts run the unpacked
+ * kernels, which need no scratch.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress); make that first
  * call before any stream capture.  All calls share the one array and each
  * solve rewrites every part of it that it reads, so nothing needs clearing;

@@ -21,6 +21,10 @@ fw_int32_conv(w32)       fw_int on the int32 I/O convention of the library
                          arithmetic in int64 with flags.
 fw_int16_conv(w16)       the same for the int16 convention (absent = 16383).
 fw_f64(w)                Fig. 1 in double precision, +inf for a missing edge.
+fw_f64_mt, fw_int32_conv_mt
+                         the same loops with the rows of each iteration k
+                         shared among host threads (all cores by default);
+                         bit-identical to the single-thread forms.
 bellman_ford_*           textbook single-source algorithm (independent pin).
 dijkstra_rows_*          textbook single-source algorithm for non-negative
                          weights, on the stored input matrix (large-n rows).
@@ -55,7 +59,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -69,6 +73,10 @@ def _load():
             i64 = ctypes.c_int64
             lib.oracle_fw_i64.argtypes = [p, p, i64]
             lib.oracle_fw_f64.argtypes = [p, i64]
+            lib.oracle_fw_i64_mt.argtypes = [p, p, i64, ctypes.c_int]
+            lib.oracle_fw_i64_mt.restype = ctypes.c_int
+            lib.oracle_fw_f64_mt.argtypes = [p, i64, ctypes.c_int]
+            lib.oracle_fw_f64_mt.restype = ctypes.c_int
             lib.oracle_bellman_ford_i64.argtypes = [p, p, i64, i64, p, p]
             lib.oracle_bellman_ford_i64.restype = ctypes.c_int
             lib.oracle_bellman_ford_f64.argtypes = [p, i64, i64, p]
@@ -124,6 +132,28 @@ def fw_f64(w: np.ndarray) -> np.ndarray:
     if d.shape[0]:
         _load().oracle_fw_f64(_ptr(d), d.shape[0])
     return d
+
+
+def fw_int32_conv_mt(w32: np.ndarray, threads: int = 0):
+    """fw_int32_conv on `threads` host threads (0 = all cores).  Returns
+    (distances, threads used)."""
+    w32 = np.asarray(w32)
+    n = w32.shape[0]
+    absent = w32 == ABSENT_I32
+    d = np.ascontiguousarray(w32, dtype=np.int64).copy()
+    inf = np.ascontiguousarray(absent, dtype=np.uint8).copy()
+    d[absent] = 0
+    used = _load().oracle_fw_i64_mt(_ptr(d), _ptr(inf), n, int(threads)) if n else 1
+    d[inf.astype(bool)] = ABSENT_I32
+    return d.astype(np.int32), used
+
+
+def fw_f64_mt(w: np.ndarray, threads: int = 0):
+    """fw_f64 on `threads` host threads (0 = all cores).  Returns (distances,
+    threads used)."""
+    d = np.ascontiguousarray(w, dtype=np.float64).copy()
+    used = _load().oracle_fw_f64_mt(_ptr(d), d.shape[0], int(threads)) if d.shape[0] else 1
+    return d, used
 
 
 # -------------------------------------------------- independent pins -------

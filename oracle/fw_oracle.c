@@ -26,6 +26,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <omp.h>
 
 /* Fig. 1 (Sec. 3.1), integer weights.  d[i*n+j] is the length, inf[i*n+j] = 1
  * marks "no path found yet".  Loop order k, i, j as printed; a candidate
@@ -63,6 +64,55 @@ void oracle_fw_f64(double *d, int64_t n)
             }
         }
     }
+}
+
+/* Fig. 1 on all host cores: the same k, i, j loop with the rows i of each
+ * iteration k shared among `threads` threads (0 = every core).  Iteration k
+ * reads row k and column k; with no negative cycle d_kk >= 0, so the
+ * candidates d_kk + d_kj and d_ik + d_kk never improve them and they do not
+ * change during iteration k.  Every thread therefore reads what the serial
+ * loop reads, and the result equals the serial one bit for bit.  Returns the
+ * number of threads used. */
+int oracle_fw_i64_mt(int64_t *d, uint8_t *inf, int64_t n, int threads)
+{
+    if (threads <= 0)
+        threads = omp_get_num_procs();
+    for (int64_t k = 0; k < n; ++k) {
+#pragma omp parallel for num_threads(threads) schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            if (inf[i * n + k])
+                continue;
+            const int64_t dik = d[i * n + k];
+            for (int64_t j = 0; j < n; ++j) {
+                if (inf[k * n + j])
+                    continue;
+                const int64_t cand = dik + d[k * n + j];
+                if (inf[i * n + j] || cand < d[i * n + j]) {
+                    d[i * n + j] = cand;
+                    inf[i * n + j] = 0;
+                }
+            }
+        }
+    }
+    return threads;
+}
+
+int oracle_fw_f64_mt(double *d, int64_t n, int threads)
+{
+    if (threads <= 0)
+        threads = omp_get_num_procs();
+    for (int64_t k = 0; k < n; ++k) {
+#pragma omp parallel for num_threads(threads) schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            const double dik = d[i * n + k];
+            for (int64_t j = 0; j < n; ++j) {
+                const double cand = dik + d[k * n + j];
+                if (cand < d[i * n + j])
+                    d[i * n + j] = cand;
+            }
+        }
+    }
+    return threads;
 }
 
 /* Bellman-Ford from one source over the dense edge list of w (textbook

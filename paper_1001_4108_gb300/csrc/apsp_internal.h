@@ -38,6 +38,10 @@ struct RunArgs {
   int64_t first_src_ld;
   void *last_dst;
   int64_t last_dst_ld;
+  // fp32: the packed phase-3 kernels must run on `ws` whenever tma_ok holds
+  // and there are two stages or more; otherwise the run returns
+  // APSP_EUNSUPPORTED before enqueueing work.
+  bool require_ws;
 };
 
 // Events a traced solve records per stage (apsp_options.events).

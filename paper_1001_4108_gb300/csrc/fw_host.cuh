@@ -161,10 +161,10 @@ static cudaError_t launch(void (*k)(KP...), dim3 grid, int threads, size_t smem,
 template <typename T, int S, bool HAS_TMA, bool VIA>
 static int run_rounds(const RunArgs &a) {
   using K = Kernels<T, S>;
-  static thread_local int setup_done_mask = 0;  // bit per device
+  static thread_local uint64_t setup_done_mask = 0;  // bit per device
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return APSP_ECUDA;
-  if (!(setup_done_mask & (1 << (dev & 31)))) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return APSP_ECUDA;
+  if (!(setup_done_mask & (1ull << dev))) {
     if (K::setup() != cudaSuccess) return APSP_ECUDA;
     if constexpr (HAS_TMA) {
       if (cudaFuncSetAttribute(fw_tile_tma<T, S, 0, VIA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -188,7 +188,7 @@ static int run_rounds(const RunArgs &a) {
           cudaFuncSetAttribute(fw_tile_s16x2<S, 1, VIA>, attr, P3S16<S>::SMEM) != cudaSuccess)
         return APSP_ECUDA;
     }
-    setup_done_mask |= 1 << (dev & 31);
+    setup_done_mask |= 1ull << dev;
   }
 
   T *d = static_cast<T *>(a.d);
@@ -245,6 +245,12 @@ static int run_rounds(const RunArgs &a) {
   if constexpr (std::is_same<T, int16_t>::value) p3_tma = use_s16;
   else p3_tma = use_tma;
   const bool needs_panel = use_packed || use_s16;
+  // A caller that supplies its workspace for the packed fp32 kernels (the
+  // allocation-free entry point) is told when they cannot run on it, before
+  // any work is enqueued, instead of getting the unpacked kernels silently.
+  if constexpr (std::is_same<T, float>::value) {
+    if (a.require_ws && a.tma_ok && !generic_only && R > 1 && !use_packed) return APSP_EUNSUPPORTED;
+  }
   const bool routed = a.first_src || a.last_dst;
   const auto aligned16 = [](const void *p, int64_t ld_) {
     return reinterpret_cast<uintptr_t>(p) % 16 == 0 && ((size_t)ld_ * sizeof(T)) % 16 == 0;

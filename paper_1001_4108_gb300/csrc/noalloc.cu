@@ -75,5 +75,11 @@ extern "C" int apsp_fw_f32_noalloc(void *dist, int64_t n, int64_t ld, void *stre
   a.tma_ok = reinterpret_cast<uintptr_t>(dist) % 16 == 0 && ((size_t)ld * sizeof(float)) % 16 == 0;
   a.ws = panel;
   a.ws_bytes = kPanelFloats * sizeof(float);
+  // One panel buffer always fits (s * ceil(n/s) * s floats <= 128 * 16384),
+  // so the solve takes the plain schedule on the static array; whenever the
+  // layout allows the packed kernels they must use it (the run refuses
+  // rather than fall back to the unpacked kernels without telling).
+  if (apsp::interleaved_panel_bytes(n, a.S) > a.ws_bytes) return APSP_EUNSUPPORTED;
+  a.require_ws = true;
   return apsp::run_f32(a);
 }

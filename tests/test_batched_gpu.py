@@ -1,6 +1,9 @@
 """Batched form (apsp_fw_batched): many graphs of uneven n in one persistent
 launch.  Integer results must be bit-identical to the oracle and to one
 apsp_fw call per graph; fp32 within the parity tolerance."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -44,6 +47,14 @@ def test_c4_full_batch_equals_per_graph_launches():
     torch.cuda.synchronize()
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+    # every one of the 4096 graphs against the oracle (Fig. 1, int64 with
+    # infinity flags), spread over the host cores: the oracle call releases
+    # the interpreter lock
+    got = [x.cpu().numpy() for x in a]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        exp = list(ex.map(oracle.fw_int32_conv, ws))
+    for k, (x, e) in enumerate(zip(got, exp)):
+        np.testing.assert_array_equal(x, e, err_msg=f"graph {k} (n = {ws[k].shape[0]})")
     # replay (second call of the same batch runs its CUDA graph)
     c = _to_gpu(ws[:300])
     for _ in range(3):

@@ -59,3 +59,11 @@ def test_serving_surfaces_submit_errors():
         assert "boom" in str(e)
     else:
         raise AssertionError("expected the submit error")
+
+
+def test_cpu_baseline_all_cores_and_single_thread():
+    # the oracle timed on every host core and on one thread, for each dtype
+    for dt in ("f32", "i32", "i16"):
+        r = bench.cpu_baseline(dt, n_sample=96)
+        assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0
+        assert r["single_thread"]["cores"] == 1 and r["single_thread"]["value"] > 0

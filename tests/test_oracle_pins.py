@@ -368,6 +368,55 @@ def test_mutants_are_caught(mutation):
         np.testing.assert_array_equal(dm, np.where(bunr, INF, bd))
 
 
+# ------------------------------------------- the all-core Fig. 1 loops ---
+
+def test_multithreaded_fig1_equals_serial():
+    """fw_int32_conv_mt / fw_f64_mt share the rows of each iteration k among
+    threads; with no negative cycle they read what the serial loop reads, so
+    they must equal the pinned serial forms bit for bit (negative edges,
+    unreachable pairs, thread counts above n included)."""
+    g = inputs.rng(700)
+    for trial in range(12):
+        n = int(g.integers(1, 90))
+        w = inputs.int_graph(n, float(g.uniform(0.02, 0.6)), 0, 1000, seed=700 + trial,
+                             potential_max=int(g.integers(0, 60)))
+        exp = oracle.fw_int32_conv(w)
+        for threads in (1, 2, 3, 0):
+            d, used = oracle.fw_int32_conv_mt(w, threads)
+            np.testing.assert_array_equal(d, exp, err_msg=f"trial {trial} threads {threads}")
+            assert used >= 1 and (threads == 0 or used == threads)
+        f, pot = inputs.dense_f32(n, seed=800 + trial, reweighted=True)
+        f[g.random((n, n)) < 0.3] = np.inf
+        np.fill_diagonal(f, 0)
+        e64 = oracle.fw_f64(f)
+        for threads in (1, 4, 0):
+            np.testing.assert_array_equal(oracle.fw_f64_mt(f, threads)[0], e64)
+
+
+@pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(GOLDEN, "g*.txt"))),
+                         ids=lambda p: os.path.basename(p))
+def test_multithreaded_fig1_golden(path):
+    kind, n, rin, rout = _parse_golden(path)
+    if kind == "int":
+        w = np.array([[INF if t == "inf" else int(t) for t in r] for r in rin], np.int32)
+        exp = np.array([[INF if t == "inf" else int(t) for t in r] for r in rout], np.int32)
+        np.testing.assert_array_equal(oracle.fw_int32_conv_mt(w, 3)[0], exp)
+    else:
+        w = np.array([[np.inf if t == "inf" else float(t) for t in r] for r in rin])
+        exp = np.array([[np.inf if t == "inf" else float(t) for t in r] for r in rout])
+        np.testing.assert_array_equal(oracle.fw_f64_mt(w, 3)[0], exp)
+
+
+def test_multithreaded_fig1_brute_force():
+    g = inputs.rng(701)
+    for trial in range(100):
+        n = int(g.integers(1, 8))
+        w, absent = _rand_int_graph(g, n, float(g.uniform(0.1, 0.9)), 0, 20, pot=int(g.integers(0, 15)))
+        w32 = np.where(absent, INF, w).astype(np.int32)
+        bd, bunr = _brute_as_arrays(oracle.brute_force_paths(w, absent))
+        np.testing.assert_array_equal(oracle.fw_int32_conv_mt(w32, 2)[0], np.where(bunr, INF, bd))
+
+
 # --------------------------------------------------- library conventions ---
 
 def test_int16_convention():

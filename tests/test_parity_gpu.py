@@ -405,6 +405,111 @@ def test_c2_reweighted_fp32(n):
     assert_fp32_close(gpu_solve(w), d64, scale)
 
 
+_ORACLE_F64 = {}
+
+
+def _fw_f64_all_cores(key, w):
+    """Fig. 1 in FP64 on every host core (bit-identical to the single-thread
+    form), cached per input for the cases that solve it more than once."""
+    if key not in _ORACLE_F64:
+        _ORACLE_F64[key] = oracle.fw_f64_mt(w)[0]
+    return _ORACLE_F64[key]
+
+
+@pytest.mark.parametrize("n", [2048, 4096])
+@pytest.mark.parametrize("kblock", [0, 128])
+def test_c2_reweighted_fp32_config_sizes(n, kblock):
+    """The negative-edge variant of the fp32 workload (w' = w + p_u - p_v) at
+    its own sizes against the full FP64 oracle, on the default tile (s = 64
+    here) and forced through the s = 128 packed kernels."""
+    w, pot = inputs.dense_f32(n, seed=n + 2, reweighted=True)
+    assert (w < 0).any()
+    d64 = _fw_f64_all_cores(("rw", n), w)
+    d0 = d64 - pot[:, None] + pot[None, :]
+    cfg = binding.query_config(n, binding.APSP_F32, kblock)
+    assert cfg.kblock == (kblock or 64)
+    assert_fp32_close(gpu_solve(w, kblock=kblock), d64, np.abs(d0) + 2 * pot.max())
+
+
+def test_c2_dense_fp32_n4096_full_oracle():
+    n = 4096
+    w = inputs.dense_f32(n, seed=n)
+    assert_fp32_close(gpu_solve(w), _fw_f64_all_cores(("plain", n), w))
+
+
+def _bellman_rows_f64(wt, t, rows):
+    """best_ij = min(w_ij, min_k w_ik + d_kj) in FP64 for the given rows, on
+    the device in column blocks (a checker of the property, not the product);
+    best_ii is set to 0 (the empty path)."""
+    n = t.shape[0]
+    out = []
+    for i in rows:
+        best = wt[i].double()
+        for k0 in range(0, n, 1024):
+            cand = (wt[i, k0:k0 + 1024].double()[:, None] + t[k0:k0 + 1024].double()).min(0).values
+            best = torch.minimum(best, cand)
+        best[int(i)] = 0.0
+        out.append(best.cpu().numpy())
+    return np.stack(out)
+
+
+def test_c2_dense_fp32_n8192_sampled():
+    n = 8192
+    w = inputs.dense_f32(n, seed=n)
+    t = torch.from_numpy(w).cuda()
+    binding.apsp_fw(t)
+    torch.cuda.synchronize()
+    rows = inputs.rng(81).choice(n, size=8, replace=False)
+    d_rows = t[torch.from_numpy(rows).cuda()].cpu().numpy()
+    exact = oracle.dijkstra_rows_f32(w, rows)
+    assert_fp32_close(d_rows, exact)
+    best = _bellman_rows_f64(torch.from_numpy(w).cuda(), t, rows[:2])
+    assert (np.abs(d_rows[:2] - best) <= FP32_RTOL * np.abs(best)).all()
+    assert (t.diagonal() == 0).all().item()
+
+
+def test_c2_reweighted_fp32_full_size():
+    """The negative-edge variant at n = 16384 on the bench's s = 128 packed
+    kernels.  Exact rows come from the oracle's Dijkstra on the graph before
+    reweighting (its weights are w' - p_u + p_v, exact, in (0,1]) and the
+    closed form d'_ij = d_ij + p_i - p_j; the Bellman equation is checked on
+    sampled rows, the triangle inequality on 10^6 triples, and the diagonal
+    is 0.  Tolerance: 1e-5 * S_ij, S_ij = |d_ij| + 2 max p bounding the sum
+    of |w'| along the path."""
+    n = 16384
+    w, pot = inputs.dense_f32(n, seed=3, reweighted=True)
+    assert binding.query_config(n, binding.APSP_F32).kblock == 128
+    t = torch.from_numpy(w).cuda()
+    binding.apsp_fw(t)
+    torch.cuda.synchronize()
+    pmax = pot.max()
+    rows = inputs.rng(82).choice(n, size=4, replace=False)
+    w0 = (w.astype(np.float64) - pot[:, None] + pot[None, :]).astype(np.float32)
+    assert w0[~np.eye(n, dtype=bool)].min() > 0
+    d0_rows = oracle.dijkstra_rows_f32(w0, rows)
+    del w0
+    exact = d0_rows + pot[rows][:, None] - pot[None, :]
+    d_rows = t[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert_fp32_close(d_rows, exact, np.abs(d0_rows) + 2 * pmax)
+    # Bellman equation: |d_ij - best_ij| <= 1e-5 (S_ij + max_k S_kj)
+    best = _bellman_rows_f64(torch.from_numpy(w).cuda(), t, rows[:2])
+    s_max = (t.double() - torch.from_numpy(pot).cuda()[:, None] + torch.from_numpy(pot).cuda()[None, :]).abs().max()
+    s_max = float(s_max) + 2 * pmax
+    s_row = np.abs(d0_rows[:2]) + 2 * pmax
+    assert (np.abs(d_rows[:2].astype(np.float64) - best) <= FP32_RTOL * (s_row + s_max)).all()
+    # triangle inequality on 10^6 sampled triples
+    g = inputs.rng(83)
+    i, j, k = (torch.from_numpy(g.integers(0, n, 1_000_000)).cuda() for _ in range(3))
+    p = torch.from_numpy(pot).cuda()
+
+    def scale(a, b):
+        return (t[a, b].double() - p[a] + p[b]).abs() + 2 * pmax
+
+    slack = FP32_RTOL * (scale(i, j) + scale(i, k) + scale(k, j))
+    assert (t[i, j].double() <= t[i, k].double() + t[k, j].double() + slack).all().item()
+    assert (t.diagonal() == 0).all().item()
+
+
 # ------------------------------------------------------------------ int16 ---
 
 @pytest.mark.parametrize("n", [1, 33, 130, 2048])
