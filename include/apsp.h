@@ -377,7 +377,9 @@ APSP_API int apsp_selftest_wait(int64_t limit_ns, void *stream);
  *          2 int16x2 DPX add-min (two relaxations per instruction),
  *          3 int32 add then min as separate instructions,
  *          4 fp32 packed add.f32x2 + three-input min (two k's per pair),
- *          5 int32 two adds + three-input DPX min (two k's).
+ *          5 int32 two adds + three-input DPX min (two k's),
+ *          6 fp32 two scalar adds + three-input min (two k's),
+ *          7 fp32 forms 4 and 6 alternating by column.
  *   iters  sweeps of the slice.
  *   blocks blocks to launch (<= 0: 2 per SM); threads must be 256.
  *   sink   device buffer of blocks*256 4-byte words (results are written so

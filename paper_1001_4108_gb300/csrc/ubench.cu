@@ -103,6 +103,10 @@ __global__ void __launch_bounds__(256, 2) ubench_kstep(int64_t iters, T *sink) {
 // then acc <- min(acc, a_k + b_k, a_k' + b_k') with one add.f32x2 and one
 // three-input min per (row, column).
 // form 5: int32, two adds + one three-input minimum per (row, column, k-pair).
+// form 6: fp32, two scalar adds + one three-input minimum per (row, column,
+// k-pair) (the adds may issue on either FMA sub-pipe).
+// form 7: fp32, the two forms alternating by column: one packed add for
+// column 2m, two scalar adds for column 2m + 1.
 template <int FORM>
 __global__ void __launch_bounds__(256, 2) ubench_kpair(int64_t iters, void *sinkv) {
   __shared__ __align__(16) float As[kRows * kKs];
@@ -148,6 +152,15 @@ __global__ void __launch_bounds__(256, 2) ubench_kpair(int64_t iters, void *sink
             const float2 s1 = __fadd2_rn(ap[r], make_float2(bq[m].z, bq[m].w));
             acc[r][2 * m] = min3f(acc[r][2 * m], s0.x, s0.y);
             acc[r][2 * m + 1] = min3f(acc[r][2 * m + 1], s1.x, s1.y);
+          } else if constexpr (FORM == 6) {
+            acc[r][2 * m] = min3f(acc[r][2 * m], __fadd_rn(ap[r].x, bq[m].x), __fadd_rn(ap[r].y, bq[m].y));
+            acc[r][2 * m + 1] =
+                min3f(acc[r][2 * m + 1], __fadd_rn(ap[r].x, bq[m].z), __fadd_rn(ap[r].y, bq[m].w));
+          } else if constexpr (FORM == 7) {
+            const float2 s0 = __fadd2_rn(ap[r], make_float2(bq[m].x, bq[m].y));
+            acc[r][2 * m] = min3f(acc[r][2 * m], s0.x, s0.y);
+            acc[r][2 * m + 1] =
+                min3f(acc[r][2 * m + 1], __fadd_rn(ap[r].x, bq[m].z), __fadd_rn(ap[r].y, bq[m].w));
           } else {
             const int32_t a0 = __float_as_int(ap[r].x), a1 = __float_as_int(ap[r].y);
             iacc[r][2 * m] = __vimin3_s32(iacc[r][2 * m], a0 + __float_as_int(bq[m].x), a1 + __float_as_int(bq[m].y));
@@ -157,7 +170,7 @@ __global__ void __launch_bounds__(256, 2) ubench_kpair(int64_t iters, void *sink
         }
     }
   }
-  if constexpr (FORM == 4) {
+  if constexpr (FORM == 4 || FORM == 6 || FORM == 7) {
     float s = 1e30f;
 #pragma unroll
     for (int r = 0; r < 8; ++r)
@@ -178,7 +191,7 @@ __global__ void __launch_bounds__(256, 2) ubench_kpair(int64_t iters, void *sink
 
 extern "C" int apsp_ubench_minplus(int form, int64_t iters, int blocks, int threads, void *sink, void *stream,
                                    double *relax_per_s) {
-  if (!sink || !relax_per_s || iters <= 0 || form < 0 || form > 5) return APSP_EINVAL;
+  if (!sink || !relax_per_s || iters <= 0 || form < 0 || form > 7) return APSP_EINVAL;
   if (threads != 256) return APSP_EINVAL;  // the micro-tile layout is fixed
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (blocks <= 0) {
@@ -201,6 +214,8 @@ extern "C" int apsp_ubench_minplus(int form, int64_t iters, int blocks, int thre
       case 3: ubench_kstep<int32_t, 3><<<blocks, 256, 0, st>>>(its, (int32_t *)sink); break;
       case 4: ubench_kpair<4><<<blocks, 256, 0, st>>>(its, sink); break;
       case 5: ubench_kpair<5><<<blocks, 256, 0, st>>>(its, sink); break;
+      case 6: ubench_kpair<6><<<blocks, 256, 0, st>>>(its, sink); break;
+      case 7: ubench_kpair<7><<<blocks, 256, 0, st>>>(its, sink); break;
     }
   };
   launch(iters / 8 + 1);  // warm-up (clocks, instruction cache)
