@@ -126,6 +126,55 @@ __device__ __forceinline__ void minplus_tile(typename Arith<T>::C (&acc)[M][M], 
   }
 }
 
+// Phase 1 inside one CTA: closes the diagonal tile (p0, p0) -- kvalid
+// sequential k steps on an M x M register block per thread, row and column
+// k + 1 published through a double buffer (one barrier per step) -- stores it
+// (clamped in the last stage) and leaves it in Ds (padded rows).  Ends with a
+// barrier.
+template <typename T, int S, int M>
+__device__ __forceinline__ void close_diag(T *d, int64_t ld, int64_t n, int64_t p0, int kvalid, bool last,
+                                           typename Arith<T>::C *Ds, typename Arith<T>::C *rowbuf,
+                                           typename Arith<T>::C *colbuf, int ty, int tx) {
+  using C = typename Arith<T>::C;
+  using IO = TileIO<T, S, M>;
+  C x[M][M];
+  IO::load(d, ld, n, p0, p0, ty, tx, x);
+  if (ty == 0)
+#pragma unroll
+    for (int c = 0; c < M; ++c) rowbuf[M * tx + c] = x[0][c];
+  if (tx == 0)
+#pragma unroll
+    for (int a = 0; a < M; ++a) colbuf[M * ty + a] = x[a][0];
+  for (int kq = 0; kq < (kvalid + M - 1) / M; ++kq) {
+#pragma unroll
+    for (int u = 0; u < M; ++u) {
+      const int k = M * kq + u;
+      __syncthreads();
+      C rk[M], ck[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) rk[c] = rowbuf[(k & 1) * S + M * tx + c];
+#pragma unroll
+      for (int a = 0; a < M; ++a) ck[a] = colbuf[(k & 1) * S + M * ty + a];
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::relax(x[a][c], ck[a], rk[c]);
+      const int k1 = k + 1;
+      if (k1 < S) {
+        if (ty == k1 / M)
+#pragma unroll
+          for (int c = 0; c < M; ++c) rowbuf[(k1 & 1) * S + M * tx + c] = x[(u + 1) % M][c];
+        if (tx == k1 / M)
+#pragma unroll
+          for (int a = 0; a < M; ++a) colbuf[(k1 & 1) * S + M * ty + a] = x[a][(u + 1) % M];
+      }
+    }
+  }
+  IO::store(d, ld, n, p0, p0, ty, tx, x, last);
+  IO::to_smem(Ds, ty, tx, x);
+  __syncthreads();
+}
+
 template <typename T, int S, int M>
 __global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDesc *__restrict__ descs, int count,
                                                                    int *counter) {
@@ -158,42 +207,7 @@ __global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDe
       const int kvalid = (int)min((int64_t)S, n - p0);  // vertices of k-block b inside the graph
       const int kq_end = (kvalid + 3) / 4;
       // ---- phase 1: close the diagonal tile (registers + row/column k broadcast)
-      C x[M][M];
-      IO::load(d, ld, n, p0, p0, ty, tx, x);
-      if (ty == 0)
-#pragma unroll
-        for (int c = 0; c < M; ++c) rowbuf[M * tx + c] = x[0][c];
-      if (tx == 0)
-#pragma unroll
-        for (int a = 0; a < M; ++a) colbuf[M * ty + a] = x[a][0];
-      for (int kq = 0; kq < (kvalid + M - 1) / M; ++kq) {
-#pragma unroll
-        for (int u = 0; u < M; ++u) {
-          const int k = M * kq + u;
-          __syncthreads();
-          C rk[M], ck[M];
-#pragma unroll
-          for (int c = 0; c < M; ++c) rk[c] = rowbuf[(k & 1) * S + M * tx + c];
-#pragma unroll
-          for (int a = 0; a < M; ++a) ck[a] = colbuf[(k & 1) * S + M * ty + a];
-#pragma unroll
-          for (int a = 0; a < M; ++a)
-#pragma unroll
-            for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::relax(x[a][c], ck[a], rk[c]);
-          const int k1 = k + 1;
-          if (k1 < S) {
-            if (ty == k1 / M)
-#pragma unroll
-              for (int c = 0; c < M; ++c) rowbuf[(k1 & 1) * S + M * tx + c] = x[(u + 1) % M][c];
-            if (tx == k1 / M)
-#pragma unroll
-              for (int a = 0; a < M; ++a) colbuf[(k1 & 1) * S + M * ty + a] = x[a][(u + 1) % M];
-          }
-        }
-      }
-      IO::store(d, ld, n, p0, p0, ty, tx, x, last);
-      IO::to_smem(Ds, ty, tx, x);
-      __syncthreads();
+      close_diag<T, S, M>(d, ld, n, p0, kvalid, last, Ds, rowbuf, colbuf, ty, tx);
       // ---- phase 2: row panel D (x) X and column panel X (x) D
       for (int t = 0; t < 2 * (R - 1); ++t) {
         const bool row = t < R - 1;
@@ -233,6 +247,255 @@ __global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDe
   }
 }
 
+// ------------------------------------------------ grouped shape (s 64, 8x8)
+// Same work split (one CTA per graph, every stage inside the CTA), but
+// phases 2 and 3 hand whole 64 x 64 tiles to four groups of 64 threads, each
+// thread holding an 8 x 8 register block of its group's tile (rows ty + 8r,
+// columns 4tx + c and 32 + 4tx + c, tx = t % 8, ty = t / 8 within the
+// group): the register-tile form of Sec. 4.1 the single-graph kernels use,
+// 64 relaxations per pair of operand loads.  Operand tiles reach shared
+// memory by cp.async (16-byte copies when every row is 16-byte aligned) and
+// each group waits only on its own named barrier; the A tile of phase 3 (the
+// column-panel tile of a tile row) is shared by the four groups.  Phase 1 is
+// the 4 x 4 register form over all 256 threads.  The per-element operations
+// are those of every other kernel (one rounded sum per candidate, exact
+// minimum), so results are bit-identical to them at s = 64.
+struct GShape {
+  static constexpr int S = 64, NT = 256, NG = 4, LD = 68;
+  static constexpr size_t TILE = (size_t)S * LD * 4;              // one padded tile, bytes
+  static constexpr size_t SMEM = 6 * TILE + 4 * (size_t)S * 4 + 16;  // Ds, As, 4 group tiles, row/col k, slot
+};
+
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 64;" ::"r"(g + 1) : "memory"); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Copies the 64 x 64 tile at (r0, c0) into shared memory (row stride LD),
+// infinity outside the matrix; `nthr` threads take part (thread t of them).
+// Interior tiles move by cp.async (the caller waits with cp_async_wait_all
+// and a barrier); edge tiles by predicated loads and shared stores.
+template <typename T>
+__device__ __forceinline__ void tile_to_smem(const T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, bool vec,
+                                             typename Arith<T>::C *dst, int t, int nthr) {
+  using C = typename Arith<T>::C;
+  constexpr int S = GShape::S, LD = GShape::LD;
+  static_assert(sizeof(T) == 4, "32-bit element types");
+  if (r0 + S <= n && c0 + S <= n) {
+    if (vec) {
+      for (int q = t; q < S * S / 4; q += nthr) {  // 16 chunks of 4 elements per row
+        const int i = q >> 4, j = (q & 15) << 2;
+        cp_async16(dst + i * LD + j, d + (r0 + i) * ld + c0 + j);
+      }
+    } else {
+      for (int e = t; e < S * S; e += nthr) {
+        const int i = e >> 6, j = e & 63;
+        cp_async4(dst + i * LD + j, d + (r0 + i) * ld + c0 + j);
+      }
+    }
+    return;
+  }
+  for (int e = t; e < S * S; e += nthr) {
+    const int i = e >> 6, j = e & 63;
+    const int64_t gi = r0 + i, gj = c0 + j;
+    dst[i * LD + j] = (gi < n && gj < n) ? Arith<T>::load(d[gi * ld + gj]) : Arith<T>::inf();
+  }
+}
+
+// C tile (r0, c0) -> the 8 x 8 register block of thread (ty, tx) of a group.
+template <typename T>
+__device__ __forceinline__ void load_block8(const T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, bool vec,
+                                            int ty, int tx, typename Arith<T>::C (&x)[8][8]) {
+  constexpr int S = GShape::S;
+  if (r0 + S <= n && c0 + S <= n) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const T *row = d + (r0 + ty + 8 * r) * ld + c0 + 4 * tx;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (vec) {
+          ld4<T>(row + 32 * h, x[r][4 * h], x[r][4 * h + 1], x[r][4 * h + 2], x[r][4 * h + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) x[r][4 * h + c] = Arith<T>::load(row[32 * h + c]);
+        }
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int64_t gi = r0 + ty + 8 * r, gj = c0 + 32 * (c / 4) + 4 * tx + (c % 4);
+      x[r][c] = (gi < n && gj < n) ? Arith<T>::load(d[gi * ld + gj]) : Arith<T>::inf();
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_block8(T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, bool vec, int ty,
+                                             int tx, const typename Arith<T>::C (&x)[8][8], bool last) {
+  constexpr int S = GShape::S;
+  if (r0 + S <= n && c0 + S <= n) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      T *row = d + (r0 + ty + 8 * r) * ld + c0 + 4 * tx;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        T v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = last ? Arith<T>::finish(x[r][4 * h + c]) : (T)x[r][4 * h + c];
+        if (vec) {
+          st4<T>(row + 32 * h, v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) row[32 * h + c] = v[c];
+        }
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int64_t gi = r0 + ty + 8 * r, gj = c0 + 32 * (c / 4) + 4 * tx + (c % 4);
+      if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(x[r][c]) : (T)x[r][c];
+    }
+}
+
+// acc <- min(acc, A (x) B) over the first 4 * kq_end k's: A rows ty + 8r,
+// B columns 4tx + c and 32 + 4tx + c, both in shared memory with row stride
+// LD (the padding k's of a partial k-block hold infinity).
+template <typename T>
+__device__ __forceinline__ void minplus_block8(typename Arith<T>::C (&acc)[8][8], const typename Arith<T>::C *A,
+                                               const typename Arith<T>::C *B, int ty, int tx, int kq_end) {
+  using C = typename Arith<T>::C;
+  constexpr int LD = GShape::LD;
+  const C *Ar = A + ty * LD;
+  const C *Bc = B + 4 * tx;
+#pragma unroll 1
+  for (int kq = 0; kq < kq_end; ++kq) {
+    C a[8][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) lds4<C>(Ar + 8 * r * LD + 4 * kq, a[r][0], a[r][1], a[r][2], a[r][3]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const C *brow = Bc + (4 * kq + u) * LD;
+      C bv[8];
+      lds4<C>(brow, bv[0], bv[1], bv[2], bv[3]);
+      lds4<C>(brow + 32, bv[4], bv[5], bv[6], bv[7]);
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = Arith<T>::relax(acc[r][c], a[r][u], bv[c]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GShape::NT, 2) fw_batched_grp(const BatchDesc *__restrict__ descs, int count,
+                                                                  int *counter) {
+  using C = typename Arith<T>::C;
+  constexpr int S = GShape::S, LD = GShape::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *Ds = reinterpret_cast<C *>(smem_raw);  // closed diagonal tile
+  C *As = Ds + S * LD;                      // phase 3: column-panel tile of the current tile row
+  C *Gs0 = As + S * LD;                     // one operand tile per group
+  C *rowbuf = Gs0 + GShape::NG * S * LD;    // [2][S]
+  C *colbuf = rowbuf + 2 * S;               // [2][S]
+  int *s_g = reinterpret_cast<int *>(colbuf + 2 * S);
+  const int tid = threadIdx.x;
+  const int grp = tid / 64, gt = tid % 64;
+  const int tx = gt % 8, ty = gt / 8;          // 8 x 8 blocks inside the group's tile
+  const int tx4 = tid % 16, ty4 = tid / 16;    // 4 x 4 blocks of phase 1
+  C *Gs = Gs0 + grp * S * LD;
+
+  while (true) {
+    if (tid == 0) *s_g = atomicAdd(counter, 1);
+    __syncthreads();
+    const int gidx = *s_g;
+    __syncthreads();
+    if (gidx >= count) return;
+    T *d = static_cast<T *>(descs[gidx].d);
+    const int64_t n = descs[gidx].n, ld = descs[gidx].ld;
+    const bool vec = reinterpret_cast<uintptr_t>(d) % 16 == 0 && ld % 4 == 0;
+    const int R = (int)((n + S - 1) / S);
+
+    for (int b = 0; b < R; ++b) {
+      const bool last = b == R - 1;
+      const int64_t p0 = (int64_t)b * S;
+      const int kvalid = (int)min((int64_t)S, n - p0);
+      const int kq_end = (kvalid + 3) / 4;
+      close_diag<T, S, 4>(d, ld, n, p0, kvalid, last, Ds, rowbuf, colbuf, ty4, tx4);
+      // ---- phase 2: the group tiles of row b (D (x) X) and column b (X (x) D)
+      for (int t = grp; t < 2 * (R - 1); t += GShape::NG) {
+        const bool row = t < R - 1;
+        const int other = skip_pivot(row ? t : t - (R - 1), b);
+        const int64_t r0 = row ? p0 : (int64_t)other * S, c0 = row ? (int64_t)other * S : p0;
+        tile_to_smem<T>(d, ld, n, r0, c0, vec, Gs, gt, 64);
+        C acc[8][8];
+        load_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc);
+        cp_async_wait_all();
+        group_sync(grp);
+        if (row)
+          minplus_block8<T>(acc, Ds, Gs, ty, tx, kq_end);
+        else
+          minplus_block8<T>(acc, Gs, Ds, ty, tx, kq_end);
+        store_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc, last);
+        group_sync(grp);
+      }
+      __syncthreads();  // panels final and visible to the CTA
+      // ---- phase 3: per tile row, A = its column-panel tile (shared), each
+      // group takes tiles of the row with B = the row-panel tile above it
+      for (int ii = 0; ii < R - 1; ++ii) {
+        const int64_t r0 = (int64_t)skip_pivot(ii, b) * S;
+        tile_to_smem<T>(d, ld, n, r0, p0, vec, As, tid, GShape::NT);
+        cp_async_wait_all();
+        __syncthreads();
+        for (int jj = grp; jj < R - 1; jj += GShape::NG) {
+          const int64_t c0 = (int64_t)skip_pivot(jj, b) * S;
+          tile_to_smem<T>(d, ld, n, p0, c0, vec, Gs, gt, 64);
+          C acc[8][8];
+          load_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc);
+          cp_async_wait_all();
+          group_sync(grp);
+          minplus_block8<T>(acc, As, Gs, ty, tx, kq_end);
+          store_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc, last);
+          group_sync(grp);
+        }
+        __syncthreads();  // As is reloaded for the next tile row
+      }
+    }
+  }
+}
+
+template <typename T>
+int launch_grouped_kernel(const BatchDesc *descs, int count, int *counter, cudaStream_t st) {
+  static thread_local uint64_t setup_mask = 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return APSP_ECUDA;
+  if (!(setup_mask & (1ull << dev))) {
+    if (cudaFuncSetAttribute(fw_batched_grp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GShape::SMEM) !=
+        cudaSuccess)
+      return APSP_ECUDA;
+    setup_mask |= 1ull << dev;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return APSP_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_grp<T>, GShape::NT, GShape::SMEM) !=
+      cudaSuccess)
+    return APSP_ECUDA;
+  const int grid = std::max(1, std::min(count, sms * std::max(per_sm, 1)));
+  if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return APSP_ECUDA;
+  fw_batched_grp<T><<<grid, GShape::NT, GShape::SMEM, st>>>(descs, count, counter);
+  return cudaPeekAtLastError() == cudaSuccess ? APSP_OK : APSP_ECUDA;
+}
+
 template <typename T, int S, int M>
 int launch_batched_kernel(const BatchDesc *descs, int count, int *counter, cudaStream_t st) {
   using B = BShape<S, M>;
@@ -262,6 +525,9 @@ int launch_variant(int variant, const BatchDesc *descs, int count, int *counter,
     case 1: return launch_batched_kernel<T, 32, 4>(descs, count, counter, st);
     case 2: return launch_batched_kernel<T, 64, 4>(descs, count, counter, st);
     case 3: return launch_batched_kernel<T, 128, 4>(descs, count, counter, st);
+    case 4:
+      if constexpr (sizeof(T) == 4) return launch_grouped_kernel<T>(descs, count, counter, st);
+      return launch_batched_kernel<T, 64, 4>(descs, count, counter, st);  // int16: the (64, 4) shape
   }
   return APSP_EINVAL;
 }
