@@ -293,15 +293,16 @@ APSP_API int apsp_tuning_load(const char *path);
  * request's host matrix and queues it; a scheduler thread of the server admits
  * queued requests oldest first while an in-flight slot is free and the
  * request's device footprint fits the HBM budget, uploads each admitted matrix
- * once and solves it on the device (fp32 requests with n <= 512 admitted
- * together share one batched launch, one CTA per graph, and so do integer ones
- * when at least 8 are admitted together; the others run on their own streams,
- * spread over all SMs, so requests overlap on the GPU), copies the result back
- * and releases the device memory.  apsp_poll / apsp_wait deliver a finished
- * result into the caller's buffer and retire the ticket.  A result is the same
- * whether the request was solved alone or among others: fp32 kernels depend
- * only on (n, dtype) and integer results are exact.  Latency is measured from
- * submit to the result being in host memory.
+ * once and solves it on the device (requests with n <= 512 share one batched
+ * launch, one CTA per graph, when at least 8 of one element type are admitted
+ * together; the others run on their own streams, spread over all SMs, so
+ * requests overlap on the GPU), copies the result back and releases the
+ * device memory.  apsp_poll / apsp_wait deliver a finished result into the
+ * caller's buffer and retire the ticket.  A result is the same whether the
+ * request was solved alone or among others: integer results are exact, and
+ * an fp32 request gets the same per-element operations in the same stage
+ * order from either kernel (tile side 64 up to n = 512).  Latency is measured
+ * from submit to the result being in host memory.
  */
 typedef struct apsp_server apsp_server;  /* opaque, owned by the library */
 

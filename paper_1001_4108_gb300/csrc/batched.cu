@@ -266,6 +266,41 @@ struct GShape {
   static constexpr size_t SMEM = 6 * TILE + 4 * (size_t)S * 4 + 16;  // Ds, As, 4 group tiles, row/col k, slot
 };
 
+// 128-bit global load / store of four 32-bit elements, and a 128-bit shared
+// load the compiler may not merge or hoist (keeps the 64 accumulators within
+// two CTAs per SM worth of registers).
+template <typename C>
+__device__ __forceinline__ void gld4(const C *p, C &x0, C &x1, C &x2, C &x3) {
+  const int4 v = *reinterpret_cast<const int4 *>(p);
+  x0 = word_as<C>(v.x);
+  x1 = word_as<C>(v.y);
+  x2 = word_as<C>(v.z);
+  x3 = word_as<C>(v.w);
+}
+template <typename C>
+__device__ __forceinline__ void gst4(C *p, C x0, C x1, C x2, C x3) {
+  *reinterpret_cast<int4 *>(p) =
+      make_int4(__builtin_bit_cast(int, x0), __builtin_bit_cast(int, x1), __builtin_bit_cast(int, x2),
+                __builtin_bit_cast(int, x3));
+}
+template <typename C>
+__device__ __forceinline__ void sld4(const C *p, C &x0, C &x1, C &x2, C &x3) {
+  int a, b, c, e;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(a), "=r"(b), "=r"(c), "=r"(e) : "r"(smem_u32(p)));
+  x0 = word_as<C>(a);
+  x1 = word_as<C>(b);
+  x2 = word_as<C>(c);
+  x3 = word_as<C>(e);
+}
+
+template <typename C>
+__device__ __forceinline__ void sld2(const C *p, C &x0, C &x1) {
+  int a, b;
+  asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "r"(smem_u32(p)));
+  x0 = word_as<C>(a);
+  x1 = word_as<C>(b);
+}
+
 __device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 64;" ::"r"(g + 1) : "memory"); }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -319,7 +354,7 @@ __device__ __forceinline__ void load_block8(const T *d, int64_t ld, int64_t n, i
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (vec) {
-          ld4<T>(row + 32 * h, x[r][4 * h], x[r][4 * h + 1], x[r][4 * h + 2], x[r][4 * h + 3]);
+          gld4<T>(row + 32 * h, x[r][4 * h], x[r][4 * h + 1], x[r][4 * h + 2], x[r][4 * h + 3]);
         } else {
 #pragma unroll
           for (int c = 0; c < 4; ++c) x[r][4 * h + c] = Arith<T>::load(row[32 * h + c]);
@@ -351,7 +386,7 @@ __device__ __forceinline__ void store_block8(T *d, int64_t ld, int64_t n, int64_
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] = last ? Arith<T>::finish(x[r][4 * h + c]) : (T)x[r][4 * h + c];
         if (vec) {
-          st4<T>(row + 32 * h, v[0], v[1], v[2], v[3]);
+          gst4<T>(row + 32 * h, v[0], v[1], v[2], v[3]);
         } else {
 #pragma unroll
           for (int c = 0; c < 4; ++c) row[32 * h + c] = v[c];
@@ -380,16 +415,16 @@ __device__ __forceinline__ void minplus_block8(typename Arith<T>::C (&acc)[8][8]
   const C *Ar = A + ty * LD;
   const C *Bc = B + 4 * tx;
 #pragma unroll 1
-  for (int kq = 0; kq < kq_end; ++kq) {
-    C a[8][4];
+  for (int kp = 0; kp < 2 * kq_end; ++kp) {  // k pairs
+    C a[8][2];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) lds4<C>(Ar + 8 * r * LD + 4 * kq, a[r][0], a[r][1], a[r][2], a[r][3]);
+    for (int r = 0; r < 8; ++r) sld2<C>(Ar + 8 * r * LD + 2 * kp, a[r][0], a[r][1]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const C *brow = Bc + (4 * kq + u) * LD;
+    for (int u = 0; u < 2; ++u) {
+      const C *brow = Bc + (2 * kp + u) * LD;
       C bv[8];
-      lds4<C>(brow, bv[0], bv[1], bv[2], bv[3]);
-      lds4<C>(brow + 32, bv[4], bv[5], bv[6], bv[7]);
+      sld4<C>(brow, bv[0], bv[1], bv[2], bv[3]);
+      sld4<C>(brow + 32, bv[4], bv[5], bv[6], bv[7]);
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -684,7 +719,7 @@ int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStr
 // stream order, then launches one persistent kernel per kernel-shape group, in
 // order, on `st`.
 int run_batched_direct(const BatchDesc *host_descs, int count, int dtype, cudaStream_t st, void **dev_buf,
-                       size_t *cap) {
+                       size_t *cap, bool match_single) {
   if (count <= 0) return APSP_OK;
   const size_t need = (size_t)count * sizeof(BatchDesc) + 16 * kBatchVariants * 2;
   if (*cap < need) {
@@ -702,11 +737,15 @@ int run_batched_direct(const BatchDesc *host_descs, int count, int dtype, cudaSt
     return APSP_ECUDA;
   const BatchDesc *dd = static_cast<const BatchDesc *>(*dev_buf);
   char *ctr = static_cast<char *>(*dev_buf) + (size_t)count * sizeof(BatchDesc);
+  auto variant_of = [&](int64_t n) {
+    const int v = tuned_batch_variant(n, dtype);
+    return match_single && n > 32 && v != 2 && v != 4 ? 2 : v;
+  };
   int first = 0, slot = 0;
   while (first < count) {
-    const int v = tuned_batch_variant(host_descs[first].n, dtype);
+    const int v = variant_of(host_descs[first].n);
     int last = first + 1;
-    while (last < count && tuned_batch_variant(host_descs[last].n, dtype) == v) ++last;
+    while (last < count && variant_of(host_descs[last].n) == v) ++last;
     const int rc = launch_dtype(dtype, v, dd + first, last - first, reinterpret_cast<int *>(ctr + 16 * slot), st);
     if (rc != APSP_OK) return rc;
     slot = (slot + 1) % (2 * kBatchVariants);

@@ -7,14 +7,17 @@
 //           in-flight slot is free and the request's device footprint fits the
 //           HBM budget; each admitted request is uploaded once and solved on
 //           its device-resident copy; requests with n <= 512 admitted together
-//           are solved by one batched launch, larger ones by the multi-CTA
-//           path on a stream of their own, so requests overlap on the device;
+//           (at least 8 of one element type) are solved by one batched
+//           launch, the others by the multi-CTA path on a stream of their
+//           own, so requests overlap on the device;
 //           the result is copied back to pinned memory, the device buffer is
 //           released in stream order, and a host callback marks completion
 //           (latency = submit -> result in host memory);
 //   poll / wait deliver the result into the caller's buffer.
-// The kernels and their configuration depend only on (n, dtype), so a
-// request's result is the same whether it is solved alone or in a mix.
+// A request's result is the same whether it is solved alone or in a mix:
+// integer results are exact, and fp32 requests get the same per-element
+// operations in the same stage order (s = 64 up to n = 512) from the batched
+// and the multi-CTA kernels.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -127,20 +130,22 @@ void fail(Request *r, int rc) {
 }
 
 // Launches admitted requests (called without s->mu).
-// Integer requests below this count in one admission round are solved one
-// by one on all SMs rather than one CTA each: the batched kernel pays off
-// when it has many graphs to spread over the SMs.  (fp32 requests always take
-// the batched kernel when small, so that their rounding never depends on the
-// load; integer results are exact either way.)
-constexpr int kMinIntBatch = 8;
+// Small requests of one element type below this count in one admission round
+// are solved one by one on all SMs rather than one CTA each: the batched
+// kernel pays off when it has many graphs to spread over the SMs.  The
+// choice never changes a result: integer results are exact either way, and
+// fp32 requests take an s = 64 batched shape, whose per-element operations
+// and stage order are those of the single-graph path at s = 64.
+constexpr int kMinBatch = 8;
 
 void launch_admitted(Server *s, std::vector<Request *> &adm) {
-  int small_int = 0;
+  int small_count[3] = {0, 0, 0};
+  auto dt_slot = [](int dtype) { return dtype == APSP_F32 ? 1 : dtype == APSP_I16 ? 2 : 0; };
   for (Request *r : adm)
-    if (r->n <= kBatchCtaMaxN && r->dtype != APSP_F32) ++small_int;
+    if (r->n <= kBatchCtaMaxN) ++small_count[dt_slot(r->dtype)];
   std::vector<Request *> small;
   for (Request *r : adm) {
-    if (r->n <= kBatchCtaMaxN && (r->dtype == APSP_F32 || small_int >= kMinIntBatch)) {
+    if (r->n <= kBatchCtaMaxN && small_count[dt_slot(r->dtype)] >= kMinBatch) {
       small.push_back(r);
       continue;
     }
@@ -153,6 +158,7 @@ void launch_admitted(Server *s, std::vector<Request *> &adm) {
     if (rc == APSP_OK) {
       apsp_options o{};
       o.flags = APSP_FLAG_NO_GRAPH;  // device addresses change from request to request
+      if (r->n <= kBatchCtaMaxN) o.kblock = 64;  // the batched kernels' depth: same result either way
       o.workspace = s->workspaces[si];
       o.workspace_bytes = s->ws_bytes;
       rc = apsp_fw_ex(r->dev, r->n, r->ld, r->dtype, &o, st);
@@ -180,7 +186,8 @@ void launch_admitted(Server *s, std::vector<Request *> &adm) {
     if (rc == APSP_OK) {
       std::vector<BatchDesc> descs;
       for (Request *r : grp) descs.push_back({r->dev, r->ld, r->n});
-      rc = run_batched_direct(descs.data(), (int)descs.size(), dt, st, &s->desc_dev, &s->desc_cap);
+      rc = run_batched_direct(descs.data(), (int)descs.size(), dt, st, &s->desc_dev, &s->desc_cap,
+                              /*match_single=*/dt == APSP_F32);
     }
     for (Request *r : grp) {
       if (rc == APSP_OK && cudaMemcpyAsync(r->host, r->dev, r->bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)

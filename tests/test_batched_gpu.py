@@ -108,7 +108,7 @@ def test_batched_padded_leading_dimension():
 def test_autotune_and_table_roundtrip(tmp_path):
     rep = binding.autotune(binding.APSP_I32)
     assert rep["dtype"] == "i32" and len(rep["batched"]) == 5 and len(rep["kblock"]) == 5
-    assert all(0 <= b["best"] < 4 and len(b["ms"]) == 4 for b in rep["batched"])
+    assert all(0 <= b["best"] < 5 and len(b["ms"]) == 5 for b in rep["batched"])
     path = str(tmp_path / "tuning.txt")
     binding.tuning_save(path)
     binding.tuning_load(path)
@@ -121,22 +121,57 @@ def test_autotune_and_table_roundtrip(tmp_path):
         np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
-def test_each_batched_shape(tmp_path, variant):
-    """Every kernel shape, forced through a tuning file for all n buckets,
-    gives the oracle's result (graphs of all buckets, ragged and whole tiles)."""
+def _force_variant(tmp_path, variant, dtypes=("i32", "f32", "i16")):
+    """Writes and loads a tuning file that gives every n bucket of the given
+    element types the batched shape `variant`; returns the saved table's path."""
     saved = str(tmp_path / "saved.txt")
     binding.tuning_save(saved)
     lines = open(saved).read().splitlines()
     forced = [lines[0]]
     for ln in lines[1:]:
         f = ln.split()
-        i = f.index("batch_variants")
-        f[i + 1:i + 6] = [str(variant)] * 5
+        if f[0] in dtypes:
+            i = f.index("batch_variants")
+            f[i + 1:i + 6] = [str(variant)] * 5
         forced.append(" ".join(f))
     path = str(tmp_path / "forced.txt")
     open(path, "w").write("\n".join(forced) + "\n")
     binding.tuning_load(path)
+    return saved
+
+
+@pytest.mark.parametrize("variant", [2, 4])
+def test_fp32_batched_s64_equals_single_graph(tmp_path, variant):
+    """The s = 64 batched shapes run the stages of the single-graph path at
+    s = 64 with the same per-element operations, so fp32 results are
+    bit-identical to apsp_fw (what lets the server pick either kernel)."""
+    saved = _force_variant(tmp_path, variant, ("f32",))
+    try:
+        g = inputs.rng(300 + variant)
+        ns = [1, 5, 33, 63, 64, 65, 100, 127, 128, 129, 200, 255, 300, 384, 449, 511, 512]
+        fs = []
+        for n in ns:
+            w, _ = inputs.dense_f32(n, seed=int(g.integers(1 << 30)), reweighted=True)
+            w[g.random((n, n)) < 0.5] = np.inf
+            np.fill_diagonal(w, 0)
+            fs.append(w)
+        tb = _to_gpu(fs)
+        binding.apsp_fw_batched(tb)
+        ts = _to_gpu(fs)
+        for t in ts:
+            binding.apsp_fw(t)
+        torch.cuda.synchronize()
+        for n, x, y in zip(ns, tb, ts):
+            assert torch.equal(x, y), n
+    finally:
+        binding.tuning_load(saved)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_each_batched_shape(tmp_path, variant):
+    """Every kernel shape, forced through a tuning file for all n buckets,
+    gives the oracle's result (graphs of all buckets, ragged and whole tiles)."""
+    saved = _force_variant(tmp_path, variant)
     try:
         g = inputs.rng(100 + variant)
         ns = [1, 17, 32, 63, 64, 100, 128, 129, 250, 256, 300, 448, 512]
@@ -146,6 +181,16 @@ def test_each_batched_shape(tmp_path, variant):
         torch.cuda.synchronize()
         for w, t in zip(ws, ts):
             np.testing.assert_array_equal(t.cpu().numpy(), oracle.fw_int32_conv(w))
+        # padded rows: 16-byte multiples (vector copies) and not
+        pads = [(130, 134), (260, 263), (333, 333), (70, 76)]
+        wp = [inputs.int_graph(n, 0.2, 0, 950, seed=n + ld, potential_max=50, ld=ld) for n, ld in pads]
+        tp = _to_gpu(wp)
+        binding.apsp_fw_batched(tp, ns=[n for n, _ in pads])
+        torch.cuda.synchronize()
+        for (n, ld), w, t in zip(pads, wp, tp):
+            out = t.cpu().numpy()
+            np.testing.assert_array_equal(out[:, :n], oracle.fw_int32_conv(np.ascontiguousarray(w[:, :n])))
+            assert (out[:, n:] == -7).all()
         fs = [inputs.dense_f32(n, seed=n) for n in (40, 200, 512)]
         tf = _to_gpu(fs)
         binding.apsp_fw_batched(tf)
