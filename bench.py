@@ -44,7 +44,7 @@ def _args():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--kblock", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--batched", type=int, default=4096, help="graphs in the batched (c4) comparison; 0 = skip")
     ap.add_argument("--serving", type=int, default=240, help="requests in the serving (c5) sweep; 0 = skip")
     ap.add_argument("--paths", type=int, default=1, help="time the solve with path bookkeeping; 0 = skip")
@@ -89,8 +89,9 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 200):
         self.gpu = gpu_index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
         self._t = None
@@ -99,7 +100,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
@@ -608,13 +609,17 @@ def measure_single(a, dtype: str, n: int, steps: int, warmup: int, e2e_steps: in
     # e2e: the host entry point (pinned host matrix -> H2D -> solve -> D2H)
     e2e = None
     if e2e_steps > 0:
+        # both host buffers pinned: no pageable memory is touched in the loop
         host = torch.from_numpy(w).pin_memory()
-        src = host.clone()
+        src = torch.empty_like(host).pin_memory()
+        src.copy_(host)
         for _ in range(2):  # warm-up: allocates the device stage, captures the graph
             host.copy_(src)
             binding.apsp_fw_host(host)
         ts, windows = [], []
-        e2e_sampler = ClockSampler(clock_gpu) if clock_gpu is not None else None
+        # one clock sample per second: the sampler's own driver queries stay
+        # out of most steps
+        e2e_sampler = ClockSampler(clock_gpu, period_ms=1000) if clock_gpu is not None else None
         if e2e_sampler:
             e2e_sampler.start()
             time.sleep(0.5)  # the first sample arrives after nvidia-smi starts

@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(GShape::NT, 2) fw_batched_grp(const BatchDesc 
   constexpr int S = GShape::S, LD = GShape::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *Ds = reinterpret_cast<C *>(smem_raw);  // closed diagonal tile
-  C *As = Ds + S * LD;                      // phase 3: column-panel tile of the current tile row
+  C *As = Ds + S * LD;                      // phase 3: column-panel tile of an even tile row (odd: Ds)
   C *Gs0 = As + S * LD;                     // one operand tile per group
   C *rowbuf = Gs0 + GShape::NG * S * LD;    // [2][S]
   C *colbuf = rowbuf + 2 * S;               // [2][S]
@@ -486,26 +486,40 @@ __global__ void __launch_bounds__(GShape::NT, 2) fw_batched_grp(const BatchDesc 
         group_sync(grp);
       }
       __syncthreads();  // panels final and visible to the CTA
-      // ---- phase 3: per tile row, A = its column-panel tile (shared), each
-      // group takes tiles of the row with B = the row-panel tile above it
-      for (int ii = 0; ii < R - 1; ++ii) {
-        const int64_t r0 = (int64_t)skip_pivot(ii, b) * S;
-        tile_to_smem<T>(d, ld, n, r0, p0, vec, As, tid, GShape::NT);
+      // ---- phase 3: the (R-1)^2 tiles in row-major order, in rounds of one
+      // tile per group.  A = the column-panel tile of the tile's row, shared
+      // by the groups: a round spans at most two consecutive tile rows, whose
+      // A tiles sit in two buffers by row parity (As, and Ds, free in phase
+      // 3); B = the row-panel tile above the tile, per group.
+      const int m = R - 1, tiles3 = m * m;
+      int held0 = -1, held1 = -1;  // tile row in As / Ds
+      for (int first = 0; first < tiles3; first += GShape::NG) {
+        const int row_a = first / m, row_b = min(first + GShape::NG - 1, tiles3 - 1) / m;
+        __syncthreads();  // the previous round is done with the A buffers
+        for (int rr = row_a; rr <= row_b; ++rr) {
+          int &held = (rr & 1) ? held1 : held0;
+          if (held != rr) {
+            tile_to_smem<T>(d, ld, n, (int64_t)skip_pivot(rr, b) * S, p0, vec, (rr & 1) ? Ds : As, tid, GShape::NT);
+            held = rr;
+          }
+        }
         cp_async_wait_all();
         __syncthreads();
-        for (int jj = grp; jj < R - 1; jj += GShape::NG) {
-          const int64_t c0 = (int64_t)skip_pivot(jj, b) * S;
+        const int item = first + grp;
+        if (item < tiles3) {
+          const int ii = item / m, jj = item % m;
+          const int64_t r0 = (int64_t)skip_pivot(ii, b) * S, c0 = (int64_t)skip_pivot(jj, b) * S;
           tile_to_smem<T>(d, ld, n, p0, c0, vec, Gs, gt, 64);
           C acc[8][8];
           load_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc);
           cp_async_wait_all();
           group_sync(grp);
-          minplus_block8<T>(acc, As, Gs, ty, tx, kq_end);
+          minplus_block8<T>(acc, (ii & 1) ? Ds : As, Gs, ty, tx, kq_end);
           store_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc, last);
           group_sync(grp);
         }
-        __syncthreads();  // As is reloaded for the next tile row
       }
+      __syncthreads();  // Ds and As are rewritten by the next stage
     }
   }
 }

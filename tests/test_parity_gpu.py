@@ -547,6 +547,22 @@ def test_int16_large_vs_int32_and_dijkstra():
     np.testing.assert_array_equal(d32[rows], oracle.dijkstra_rows_i32(w32, rows))
 
 
+@pytest.mark.parametrize("n", [5200, 6144])
+def test_int16_bulk_two_tiles_per_cta(n):
+    """s = 128 int16x2 bulk launches take two tiles per CTA (odd and even
+    tile counts, ragged and whole): identical to the int32 path, to the
+    reversed k order and to exact Dijkstra rows."""
+    w32 = inputs.int_graph(n, 0.05, 1, 3, seed=n)
+    w16 = inputs.to_int16(w32)
+    assert binding.query_config(n, binding.APSP_I16).kblock == 128
+    d16 = gpu_solve(w16)
+    np.testing.assert_array_equal(gpu_solve(w16, flags=binding.FLAG_REVERSE_K), d16)
+    d32 = gpu_solve(w32)
+    np.testing.assert_array_equal(np.where(d16 == inputs.INF_I16, INF, d16.astype(np.int32)), d32)
+    rows = [0, n // 2, n - 1]
+    np.testing.assert_array_equal(d32[rows], oracle.dijkstra_rows_i32(w32, rows))
+
+
 # --------------------------------------------------------------- host path ---
 
 def test_host_entry_point():
