@@ -98,11 +98,11 @@ int run_batched_small(const BatchDesc *host_descs, int count, int dtype, cudaStr
 
 // Autotuned choices (defaults until apsp_autotune / apsp_tuning_load).
 // Batched kernel shapes: 0 = (s 32, 2x2), 1 = (s 32, 4x4), 2 = (s 64, 4x4),
-// 3 = (s 128, 4x4), 4 = (s 64, 8x8 in four thread groups; int16: as 2).
-constexpr int kBatchVariants = 5;
+// 3 = (s 128, 4x4).
+constexpr int kBatchVariants = 4;
 int tuned_batch_variant(int64_t n, int dtype);
 int tuned_kblock(int64_t n, int dtype);
-// match_single: graphs with n > 32 take an s = 64 shape, so that each result
+// match_single: graphs with n > 32 take the s = 64 shape, so that each result
 // is bit-identical to apsp_fw's for that graph (s = 64 up to n = 512, and the
 // same per-element operations in every kernel).
 int run_batched_direct(const BatchDesc *host_descs, int count, int dtype, cudaStream_t st, void **dev_buf,

@@ -25,17 +25,43 @@ template <int S, int M> struct BShape {
   static constexpr int NT = Q * Q;
   static constexpr int LD = S + 4;                // padded shared-memory row stride
   static constexpr size_t SMEM = 3 * (size_t)S * LD * 4 + 4 * (size_t)S * 4 + 16;
+  // CTAs per SM the register budget is sized for (s 64: three, as the
+  // shared memory allows; 0 = no bound)
+  static constexpr int MIN_BLOCKS = S == 64 ? 3 : 0;
 };
 
+// Reinterprets a 32-bit word as the compute type (int32 or fp32).
+template <typename C> __device__ __forceinline__ C word_as(int v);
+template <> __device__ __forceinline__ int32_t word_as<int32_t>(int v) { return v; }
+template <> __device__ __forceinline__ float word_as<float>(int v) { return __int_as_float(v); }
+
+// Global <-> register moves of one S x S tile, M x M elements per thread
+// (rows M ty + a, columns M tx + c).  `vec`: 32-bit elements, 16-byte
+// aligned matrix and rows (ld % 4 == 0), so that with M = 4 each row of a
+// thread's block moves as one 128-bit access.
 template <typename T, int S, int M>
 struct TileIO {
   using C = typename Arith<T>::C;
   static constexpr int LD = BShape<S, M>::LD;
   // A tile entirely inside the matrix needs no masks (the common case).
+  static constexpr bool kVec = M == 4 && sizeof(T) == 4;
   __device__ static void load(const T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, int ty, int tx,
-                              C (&x)[M][M]) {
+                              C (&x)[M][M], bool vec) {
     if (r0 + S <= n && c0 + S <= n) {
       const T *p = d + (r0 + M * ty) * ld + c0 + M * tx;
+      if constexpr (kVec) {
+        if (vec) {
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            const int4 v = *reinterpret_cast<const int4 *>(p + a * ld);
+            x[a][0] = word_as<C>(v.x);
+            x[a][1] = word_as<C>(v.y);
+            x[a][2] = word_as<C>(v.z);
+            x[a][3] = word_as<C>(v.w);
+          }
+          return;
+        }
+      }
 #pragma unroll
       for (int a = 0; a < M; ++a)
 #pragma unroll
@@ -51,9 +77,23 @@ struct TileIO {
       }
   }
   __device__ static void store(T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, int ty, int tx,
-                               const C (&x)[M][M], bool last) {
+                               const C (&x)[M][M], bool last, bool vec) {
     if (r0 + S <= n && c0 + S <= n) {
       T *p = d + (r0 + M * ty) * ld + c0 + M * tx;
+      if constexpr (kVec) {
+        if (vec) {
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            C v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = last ? Arith<T>::finish(x[a][c]) : x[a][c];
+            *reinterpret_cast<int4 *>(p + a * ld) =
+                make_int4(__builtin_bit_cast(int, v[0]), __builtin_bit_cast(int, v[1]),
+                          __builtin_bit_cast(int, v[2]), __builtin_bit_cast(int, v[3]));
+          }
+          return;
+        }
+      }
 #pragma unroll
       for (int a = 0; a < M; ++a)
 #pragma unroll
@@ -70,16 +110,19 @@ struct TileIO {
   }
   __device__ static void to_smem(C *s, int ty, int tx, const C (&x)[M][M]) {
 #pragma unroll
-    for (int a = 0; a < M; ++a)
+    for (int a = 0; a < M; ++a) {
+      if constexpr (M == 4 && sizeof(C) == 4) {  // 16-byte aligned: padded rows of S + 4 words
+        *reinterpret_cast<int4 *>(s + (M * ty + a) * LD + M * tx) =
+            make_int4(__builtin_bit_cast(int, x[a][0]), __builtin_bit_cast(int, x[a][1]),
+                      __builtin_bit_cast(int, x[a][2]), __builtin_bit_cast(int, x[a][3]));
+      } else {
 #pragma unroll
-      for (int c = 0; c < M; ++c) s[(M * ty + a) * LD + M * tx + c] = x[a][c];
+        for (int c = 0; c < M; ++c) s[(M * ty + a) * LD + M * tx + c] = x[a][c];
+      }
+    }
   }
 };
 
-// Reinterprets a 32-bit word as the compute type (int32 or fp32).
-template <typename C> __device__ __forceinline__ C word_as(int v);
-template <> __device__ __forceinline__ int32_t word_as<int32_t>(int v) { return v; }
-template <> __device__ __forceinline__ float word_as<float>(int v) { return __int_as_float(v); }
 
 // acc[a][c] <- min(acc[a][c], min_k A[M ty + a][k] + B[k][M tx + c]) over the
 // first 4 * kq_end k's of the tile (the k-block's vertices inside the graph,
@@ -133,12 +176,12 @@ __device__ __forceinline__ void minplus_tile(typename Arith<T>::C (&acc)[M][M], 
 // barrier.
 template <typename T, int S, int M>
 __device__ __forceinline__ void close_diag(T *d, int64_t ld, int64_t n, int64_t p0, int kvalid, bool last,
-                                           typename Arith<T>::C *Ds, typename Arith<T>::C *rowbuf,
+                                           bool vec, typename Arith<T>::C *Ds, typename Arith<T>::C *rowbuf,
                                            typename Arith<T>::C *colbuf, int ty, int tx) {
   using C = typename Arith<T>::C;
   using IO = TileIO<T, S, M>;
   C x[M][M];
-  IO::load(d, ld, n, p0, p0, ty, tx, x);
+  IO::load(d, ld, n, p0, p0, ty, tx, x, vec);
   if (ty == 0)
 #pragma unroll
     for (int c = 0; c < M; ++c) rowbuf[M * tx + c] = x[0][c];
@@ -170,13 +213,14 @@ __device__ __forceinline__ void close_diag(T *d, int64_t ld, int64_t n, int64_t 
       }
     }
   }
-  IO::store(d, ld, n, p0, p0, ty, tx, x, last);
+  IO::store(d, ld, n, p0, p0, ty, tx, x, last, vec);
   IO::to_smem(Ds, ty, tx, x);
   __syncthreads();
 }
 
 template <typename T, int S, int M>
-__global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDesc *__restrict__ descs, int count,
+__global__ void __launch_bounds__(BShape<S, M>::NT, BShape<S, M>::MIN_BLOCKS)
+    fw_batched_cta(const BatchDesc *__restrict__ descs, int count,
                                                                    int *counter) {
   using C = typename Arith<T>::C;
   using IO = TileIO<T, S, M>;
@@ -199,6 +243,7 @@ __global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDe
     if (g >= count) return;
     T *d = static_cast<T *>(descs[g].d);
     const int64_t n = descs[g].n, ld = descs[g].ld;
+    const bool vec = IO::kVec && reinterpret_cast<uintptr_t>(d) % 16 == 0 && ld % 4 == 0;
     const int R = (int)((n + S - 1) / S);
 
     for (int b = 0; b < R; ++b) {
@@ -207,342 +252,44 @@ __global__ void __launch_bounds__(BShape<S, M>::NT) fw_batched_cta(const BatchDe
       const int kvalid = (int)min((int64_t)S, n - p0);  // vertices of k-block b inside the graph
       const int kq_end = (kvalid + 3) / 4;
       // ---- phase 1: close the diagonal tile (registers + row/column k broadcast)
-      close_diag<T, S, M>(d, ld, n, p0, kvalid, last, Ds, rowbuf, colbuf, ty, tx);
+      close_diag<T, S, M>(d, ld, n, p0, kvalid, last, vec, Ds, rowbuf, colbuf, ty, tx);
       // ---- phase 2: row panel D (x) X and column panel X (x) D
       for (int t = 0; t < 2 * (R - 1); ++t) {
         const bool row = t < R - 1;
         const int other = skip_pivot(row ? t : t - (R - 1), b);
         const int64_t r0 = row ? p0 : (int64_t)other * S, c0 = row ? (int64_t)other * S : p0;
         C acc[M][M];
-        IO::load(d, ld, n, r0, c0, ty, tx, acc);
+        IO::load(d, ld, n, r0, c0, ty, tx, acc, vec);
         IO::to_smem(Ps, ty, tx, acc);
         __syncthreads();
         if (row)
           minplus_tile<T, S, M>(acc, Ds, Ps, ty, tx, kq_end);
         else
           minplus_tile<T, S, M>(acc, Ps, Ds, ty, tx, kq_end);
-        IO::store(d, ld, n, r0, c0, ty, tx, acc, last);
+        IO::store(d, ld, n, r0, c0, ty, tx, acc, last, vec);
         __syncthreads();
       }
       // ---- phase 3: every other tile, A = column panel tile, B = row panel tile
       for (int ii = 0; ii < R - 1; ++ii) {
         const int64_t r0 = (int64_t)skip_pivot(ii, b) * S;
         C a[M][M];
-        IO::load(d, ld, n, r0, p0, ty, tx, a);
+        IO::load(d, ld, n, r0, p0, ty, tx, a, vec);
         IO::to_smem(Ps, ty, tx, a);
         for (int jj = 0; jj < R - 1; ++jj) {
           const int64_t c0 = (int64_t)skip_pivot(jj, b) * S;
           C bt[M][M], acc[M][M];
-          IO::load(d, ld, n, p0, c0, ty, tx, bt);
-          IO::load(d, ld, n, r0, c0, ty, tx, acc);
+          IO::load(d, ld, n, p0, c0, ty, tx, bt, vec);
+          IO::load(d, ld, n, r0, c0, ty, tx, acc, vec);
           IO::to_smem(Qs, ty, tx, bt);
           __syncthreads();
           minplus_tile<T, S, M>(acc, Ps, Qs, ty, tx, kq_end);
-          IO::store(d, ld, n, r0, c0, ty, tx, acc, last);
+          IO::store(d, ld, n, r0, c0, ty, tx, acc, last, vec);
           __syncthreads();
         }
       }
       __syncthreads();
     }
   }
-}
-
-// ------------------------------------------------ grouped shape (s 64, 8x8)
-// Same work split (one CTA per graph, every stage inside the CTA), but
-// phases 2 and 3 hand whole 64 x 64 tiles to four groups of 64 threads, each
-// thread holding an 8 x 8 register block of its group's tile (rows ty + 8r,
-// columns 4tx + c and 32 + 4tx + c, tx = t % 8, ty = t / 8 within the
-// group): the register-tile form of Sec. 4.1 the single-graph kernels use,
-// 64 relaxations per pair of operand loads.  Operand tiles reach shared
-// memory by cp.async (16-byte copies when every row is 16-byte aligned) and
-// each group waits only on its own named barrier; the A tile of phase 3 (the
-// column-panel tile of a tile row) is shared by the four groups.  Phase 1 is
-// the 4 x 4 register form over all 256 threads.  The per-element operations
-// are those of every other kernel (one rounded sum per candidate, exact
-// minimum), so results are bit-identical to them at s = 64.
-struct GShape {
-  static constexpr int S = 64, NT = 256, NG = 4, LD = 68;
-  static constexpr size_t TILE = (size_t)S * LD * 4;              // one padded tile, bytes
-  static constexpr size_t SMEM = 6 * TILE + 4 * (size_t)S * 4 + 16;  // Ds, As, 4 group tiles, row/col k, slot
-};
-
-// 128-bit global load / store of four 32-bit elements, and a 128-bit shared
-// load the compiler may not merge or hoist (keeps the 64 accumulators within
-// two CTAs per SM worth of registers).
-template <typename C>
-__device__ __forceinline__ void gld4(const C *p, C &x0, C &x1, C &x2, C &x3) {
-  const int4 v = *reinterpret_cast<const int4 *>(p);
-  x0 = word_as<C>(v.x);
-  x1 = word_as<C>(v.y);
-  x2 = word_as<C>(v.z);
-  x3 = word_as<C>(v.w);
-}
-template <typename C>
-__device__ __forceinline__ void gst4(C *p, C x0, C x1, C x2, C x3) {
-  *reinterpret_cast<int4 *>(p) =
-      make_int4(__builtin_bit_cast(int, x0), __builtin_bit_cast(int, x1), __builtin_bit_cast(int, x2),
-                __builtin_bit_cast(int, x3));
-}
-template <typename C>
-__device__ __forceinline__ void sld4(const C *p, C &x0, C &x1, C &x2, C &x3) {
-  int a, b, c, e;
-  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(a), "=r"(b), "=r"(c), "=r"(e) : "r"(smem_u32(p)));
-  x0 = word_as<C>(a);
-  x1 = word_as<C>(b);
-  x2 = word_as<C>(c);
-  x3 = word_as<C>(e);
-}
-
-template <typename C>
-__device__ __forceinline__ void sld2(const C *p, C &x0, C &x1) {
-  int a, b;
-  asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "r"(smem_u32(p)));
-  x0 = word_as<C>(a);
-  x1 = word_as<C>(b);
-}
-
-__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 64;" ::"r"(g + 1) : "memory"); }
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Copies the 64 x 64 tile at (r0, c0) into shared memory (row stride LD),
-// infinity outside the matrix; `nthr` threads take part (thread t of them).
-// Interior tiles move by cp.async (the caller waits with cp_async_wait_all
-// and a barrier); edge tiles by predicated loads and shared stores.
-template <typename T>
-__device__ __forceinline__ void tile_to_smem(const T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, bool vec,
-                                             typename Arith<T>::C *dst, int t, int nthr) {
-  using C = typename Arith<T>::C;
-  constexpr int S = GShape::S, LD = GShape::LD;
-  static_assert(sizeof(T) == 4, "32-bit element types");
-  if (r0 + S <= n && c0 + S <= n) {
-    if (vec) {
-      for (int q = t; q < S * S / 4; q += nthr) {  // 16 chunks of 4 elements per row
-        const int i = q >> 4, j = (q & 15) << 2;
-        cp_async16(dst + i * LD + j, d + (r0 + i) * ld + c0 + j);
-      }
-    } else {
-      for (int e = t; e < S * S; e += nthr) {
-        const int i = e >> 6, j = e & 63;
-        cp_async4(dst + i * LD + j, d + (r0 + i) * ld + c0 + j);
-      }
-    }
-    return;
-  }
-  for (int e = t; e < S * S; e += nthr) {
-    const int i = e >> 6, j = e & 63;
-    const int64_t gi = r0 + i, gj = c0 + j;
-    dst[i * LD + j] = (gi < n && gj < n) ? Arith<T>::load(d[gi * ld + gj]) : Arith<T>::inf();
-  }
-}
-
-// C tile (r0, c0) -> the 8 x 8 register block of thread (ty, tx) of a group.
-template <typename T>
-__device__ __forceinline__ void load_block8(const T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, bool vec,
-                                            int ty, int tx, typename Arith<T>::C (&x)[8][8]) {
-  constexpr int S = GShape::S;
-  if (r0 + S <= n && c0 + S <= n) {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const T *row = d + (r0 + ty + 8 * r) * ld + c0 + 4 * tx;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (vec) {
-          gld4<T>(row + 32 * h, x[r][4 * h], x[r][4 * h + 1], x[r][4 * h + 2], x[r][4 * h + 3]);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) x[r][4 * h + c] = Arith<T>::load(row[32 * h + c]);
-        }
-      }
-    }
-    return;
-  }
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int64_t gi = r0 + ty + 8 * r, gj = c0 + 32 * (c / 4) + 4 * tx + (c % 4);
-      x[r][c] = (gi < n && gj < n) ? Arith<T>::load(d[gi * ld + gj]) : Arith<T>::inf();
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void store_block8(T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, bool vec, int ty,
-                                             int tx, const typename Arith<T>::C (&x)[8][8], bool last) {
-  constexpr int S = GShape::S;
-  if (r0 + S <= n && c0 + S <= n) {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      T *row = d + (r0 + ty + 8 * r) * ld + c0 + 4 * tx;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        T v[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = last ? Arith<T>::finish(x[r][4 * h + c]) : (T)x[r][4 * h + c];
-        if (vec) {
-          gst4<T>(row + 32 * h, v[0], v[1], v[2], v[3]);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) row[32 * h + c] = v[c];
-        }
-      }
-    }
-    return;
-  }
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int64_t gi = r0 + ty + 8 * r, gj = c0 + 32 * (c / 4) + 4 * tx + (c % 4);
-      if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(x[r][c]) : (T)x[r][c];
-    }
-}
-
-// acc <- min(acc, A (x) B) over the first 4 * kq_end k's: A rows ty + 8r,
-// B columns 4tx + c and 32 + 4tx + c, both in shared memory with row stride
-// LD (the padding k's of a partial k-block hold infinity).
-template <typename T>
-__device__ __forceinline__ void minplus_block8(typename Arith<T>::C (&acc)[8][8], const typename Arith<T>::C *A,
-                                               const typename Arith<T>::C *B, int ty, int tx, int kq_end) {
-  using C = typename Arith<T>::C;
-  constexpr int LD = GShape::LD;
-  const C *Ar = A + ty * LD;
-  const C *Bc = B + 4 * tx;
-#pragma unroll 1
-  for (int kp = 0; kp < 2 * kq_end; ++kp) {  // k pairs
-    C a[8][2];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) sld2<C>(Ar + 8 * r * LD + 2 * kp, a[r][0], a[r][1]);
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const C *brow = Bc + (2 * kp + u) * LD;
-      C bv[8];
-      sld4<C>(brow, bv[0], bv[1], bv[2], bv[3]);
-      sld4<C>(brow + 32, bv[4], bv[5], bv[6], bv[7]);
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = Arith<T>::relax(acc[r][c], a[r][u], bv[c]);
-    }
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(GShape::NT, 2) fw_batched_grp(const BatchDesc *__restrict__ descs, int count,
-                                                                  int *counter) {
-  using C = typename Arith<T>::C;
-  constexpr int S = GShape::S, LD = GShape::LD;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *Ds = reinterpret_cast<C *>(smem_raw);  // closed diagonal tile
-  C *As = Ds + S * LD;                      // phase 3: column-panel tile of an even tile row (odd: Ds)
-  C *Gs0 = As + S * LD;                     // one operand tile per group
-  C *rowbuf = Gs0 + GShape::NG * S * LD;    // [2][S]
-  C *colbuf = rowbuf + 2 * S;               // [2][S]
-  int *s_g = reinterpret_cast<int *>(colbuf + 2 * S);
-  const int tid = threadIdx.x;
-  const int grp = tid / 64, gt = tid % 64;
-  const int tx = gt % 8, ty = gt / 8;          // 8 x 8 blocks inside the group's tile
-  const int tx4 = tid % 16, ty4 = tid / 16;    // 4 x 4 blocks of phase 1
-  C *Gs = Gs0 + grp * S * LD;
-
-  while (true) {
-    if (tid == 0) *s_g = atomicAdd(counter, 1);
-    __syncthreads();
-    const int gidx = *s_g;
-    __syncthreads();
-    if (gidx >= count) return;
-    T *d = static_cast<T *>(descs[gidx].d);
-    const int64_t n = descs[gidx].n, ld = descs[gidx].ld;
-    const bool vec = reinterpret_cast<uintptr_t>(d) % 16 == 0 && ld % 4 == 0;
-    const int R = (int)((n + S - 1) / S);
-
-    for (int b = 0; b < R; ++b) {
-      const bool last = b == R - 1;
-      const int64_t p0 = (int64_t)b * S;
-      const int kvalid = (int)min((int64_t)S, n - p0);
-      const int kq_end = (kvalid + 3) / 4;
-      close_diag<T, S, 4>(d, ld, n, p0, kvalid, last, Ds, rowbuf, colbuf, ty4, tx4);
-      // ---- phase 2: the group tiles of row b (D (x) X) and column b (X (x) D)
-      for (int t = grp; t < 2 * (R - 1); t += GShape::NG) {
-        const bool row = t < R - 1;
-        const int other = skip_pivot(row ? t : t - (R - 1), b);
-        const int64_t r0 = row ? p0 : (int64_t)other * S, c0 = row ? (int64_t)other * S : p0;
-        tile_to_smem<T>(d, ld, n, r0, c0, vec, Gs, gt, 64);
-        C acc[8][8];
-        load_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc);
-        cp_async_wait_all();
-        group_sync(grp);
-        if (row)
-          minplus_block8<T>(acc, Ds, Gs, ty, tx, kq_end);
-        else
-          minplus_block8<T>(acc, Gs, Ds, ty, tx, kq_end);
-        store_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc, last);
-        group_sync(grp);
-      }
-      __syncthreads();  // panels final and visible to the CTA
-      // ---- phase 3: the (R-1)^2 tiles in row-major order, in rounds of one
-      // tile per group.  A = the column-panel tile of the tile's row, shared
-      // by the groups: a round spans at most two consecutive tile rows, whose
-      // A tiles sit in two buffers by row parity (As, and Ds, free in phase
-      // 3); B = the row-panel tile above the tile, per group.
-      const int m = R - 1, tiles3 = m * m;
-      int held0 = -1, held1 = -1;  // tile row in As / Ds
-      for (int first = 0; first < tiles3; first += GShape::NG) {
-        const int row_a = first / m, row_b = min(first + GShape::NG - 1, tiles3 - 1) / m;
-        __syncthreads();  // the previous round is done with the A buffers
-        for (int rr = row_a; rr <= row_b; ++rr) {
-          int &held = (rr & 1) ? held1 : held0;
-          if (held != rr) {
-            tile_to_smem<T>(d, ld, n, (int64_t)skip_pivot(rr, b) * S, p0, vec, (rr & 1) ? Ds : As, tid, GShape::NT);
-            held = rr;
-          }
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        const int item = first + grp;
-        if (item < tiles3) {
-          const int ii = item / m, jj = item % m;
-          const int64_t r0 = (int64_t)skip_pivot(ii, b) * S, c0 = (int64_t)skip_pivot(jj, b) * S;
-          tile_to_smem<T>(d, ld, n, p0, c0, vec, Gs, gt, 64);
-          C acc[8][8];
-          load_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc);
-          cp_async_wait_all();
-          group_sync(grp);
-          minplus_block8<T>(acc, (ii & 1) ? Ds : As, Gs, ty, tx, kq_end);
-          store_block8<T>(d, ld, n, r0, c0, vec, ty, tx, acc, last);
-          group_sync(grp);
-        }
-      }
-      __syncthreads();  // Ds and As are rewritten by the next stage
-    }
-  }
-}
-
-template <typename T>
-int launch_grouped_kernel(const BatchDesc *descs, int count, int *counter, cudaStream_t st) {
-  static thread_local uint64_t setup_mask = 0;
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return APSP_ECUDA;
-  if (!(setup_mask & (1ull << dev))) {
-    if (cudaFuncSetAttribute(fw_batched_grp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GShape::SMEM) !=
-        cudaSuccess)
-      return APSP_ECUDA;
-    setup_mask |= 1ull << dev;
-  }
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return APSP_ECUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_grp<T>, GShape::NT, GShape::SMEM) !=
-      cudaSuccess)
-    return APSP_ECUDA;
-  const int grid = std::max(1, std::min(count, sms * std::max(per_sm, 1)));
-  if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return APSP_ECUDA;
-  fw_batched_grp<T><<<grid, GShape::NT, GShape::SMEM, st>>>(descs, count, counter);
-  return cudaPeekAtLastError() == cudaSuccess ? APSP_OK : APSP_ECUDA;
 }
 
 template <typename T, int S, int M>
@@ -574,9 +321,6 @@ int launch_variant(int variant, const BatchDesc *descs, int count, int *counter,
     case 1: return launch_batched_kernel<T, 32, 4>(descs, count, counter, st);
     case 2: return launch_batched_kernel<T, 64, 4>(descs, count, counter, st);
     case 3: return launch_batched_kernel<T, 128, 4>(descs, count, counter, st);
-    case 4:
-      if constexpr (sizeof(T) == 4) return launch_grouped_kernel<T>(descs, count, counter, st);
-      return launch_batched_kernel<T, 64, 4>(descs, count, counter, st);  // int16: the (64, 4) shape
   }
   return APSP_EINVAL;
 }
@@ -753,7 +497,7 @@ int run_batched_direct(const BatchDesc *host_descs, int count, int dtype, cudaSt
   char *ctr = static_cast<char *>(*dev_buf) + (size_t)count * sizeof(BatchDesc);
   auto variant_of = [&](int64_t n) {
     const int v = tuned_batch_variant(n, dtype);
-    return match_single && n > 32 && v != 2 && v != 4 ? 2 : v;
+    return match_single && n > 32 && v != 2 ? 2 : v;
   };
   int first = 0, slot = 0;
   while (first < count) {

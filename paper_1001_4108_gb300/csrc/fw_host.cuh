@@ -187,10 +187,6 @@ static int run_rounds(const RunArgs &a) {
       if (cudaFuncSetAttribute(fw_tile_s16x2<S, 0, VIA>, attr, P3S16<S>::SMEM_P3) != cudaSuccess ||
           cudaFuncSetAttribute(fw_tile_s16x2<S, 1, VIA>, attr, P3S16<S>::SMEM) != cudaSuccess)
         return APSP_ECUDA;
-      if constexpr (S == 128) {
-        if (cudaFuncSetAttribute(fw_tile_s16x2_pair<S, VIA>, attr, P3S16<S>::SMEM_P3) != cudaSuccess)
-          return APSP_ECUDA;
-      }
     }
     setup_done_mask |= 1ull << dev;
   }
@@ -335,14 +331,6 @@ static int run_rounds(const RunArgs &a) {
         if (use_s16) {
           const TileSet ts = make_tileset(kind, kPartAny, b, R, ragged);
           if (ts.total() == 0) return cudaSuccess;
-          if constexpr (S == 128) {
-            // the bulk launches: two tiles per CTA (the cross launch stays
-            // one tile per CTA: it is on the stage's critical path)
-            if (kind != kTilesCross)
-              return launch(fw_tile_s16x2_pair<S, VIA>, dim3((ts.total() + 1) / 2), P3S16<S>::TPB,
-                            P3S16<S>::SMEM_P3, s, prio, mArep[buf_of(b)], mB16, mC16, reinterpret_cast<int16_t *>(d),
-                            n, ld, b, ts, ts.total(), reverse, a.via, a.via_ld, a.err);
-          }
           return launch(fw_tile_s16x2<S, 0, VIA>, dim3(ts.total()), P3S16<S>::TPB, P3S16<S>::SMEM_P3, s, prio,
                         mArep[buf_of(b)], mB16, mC16, reinterpret_cast<int16_t *>(d), n, ld, b, R, ts, reverse,
                         arep[buf_of(b)], a.via, a.via_ld, a.err);

@@ -1150,171 +1150,4 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
   }
 }
 
-// TMA issue of the pair kernel: k-slice g of the CTA (tile g / NSL, slice
-// g % NSL) into ring stage st, and the C tile of tile t.
-template <int S>
-__device__ __forceinline__ void s16_pair_issue(const CUtensorMap *tmA, const CUtensorMap *tmB, unsigned char *As,
-                                               unsigned char *Bs, uint64_t *full, const int *tile_ij, int k0, int g,
-                                               int st) {
-  using P = P3S16<S>;
-  const int t = g / P::NSL, sl = g % P::NSL;
-  const int i0 = lds_volatile(tile_ij + 2 * t) * S, j0 = lds_volatile(tile_ij + 2 * t + 1) * S;
-  mbar_arrive_expect_tx(&full[st], P::A_BYTES_REP + P::B_BYTES);
-  tma_load_2d(As + st * P::A_BYTES_REP, tmA, &full[st], sl * P::KS, i0);  // workspace: x = k within block
-  tma_load_2d(Bs + st * P::B_BYTES, tmB, &full[st], j0, k0 + sl * P::KS);
-}
-template <int S>
-__device__ __forceinline__ void s16_pair_issue_c(const CUtensorMap *tmC, unsigned char *Cs, uint64_t *cbar,
-                                                 const int *tile_ij, int t) {
-  mbar_arrive_expect_tx(cbar, P3S16<S>::C_BYTES);
-  tma_load_2d(Cs, tmC, cbar, lds_volatile(tile_ij + 2 * t + 1) * S, lds_volatile(tile_ij + 2 * t) * S);
-}
-
-// Phase 3 of the int16x2 path (s = 128, deferred C), two tiles per CTA:
-// tiles 2 blockIdx.x and 2 blockIdx.x + 1 of the tile set.  The TMA ring
-// runs on across the tile boundary (the second tile's first slices are
-// issued while the first tile's last slices are consumed), and the second
-// tile's C copy starts as soon as the first tile's C has been folded, so the
-// wait for a tile's first slice is paid once per CTA instead of once per
-// tile.  Per element the same operations as fw_tile_s16x2<S, 0>.
-template <int S, bool VIA = false>
-__global__ void __launch_bounds__(P3S16<S>::TPB, 2)
-    fw_tile_s16x2_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                       const __grid_constant__ CUtensorMap tmC, int16_t *__restrict__ d, int64_t n, int64_t ld,
-                       int b, const TileSet ts, int ntiles, int reverse, int16_t *__restrict__ via, int64_t via_ld,
-                       int *err) {
-  using P = P3S16<S>;
-  static_assert(P::C_SMEM, "deferred C tile: s = 128");
-  constexpr int G = P::G;
-  constexpr int KS = P::KS;
-  constexpr int A_BYTES = P::A_BYTES_REP;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char *base =
-      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char *As = base;
-  unsigned char *Bs = base + P::STAGES * A_BYTES;
-  unsigned char *Cs = Bs + P::STAGES * P::B_BYTES;
-  uint64_t *full = reinterpret_cast<uint64_t *>(Cs + P::C_BYTES);
-  uint64_t *cbar = full + P::STAGES;
-  int *tile_ij = reinterpret_cast<int *>(cbar + 1);  // (It, Jt) of the CTA's tiles
-
-  const int tid = threadIdx.x;
-  const int tx = tid % G, ty = tid / G;
-  const int first = 2 * (int)blockIdx.x;
-  const int nt = min(2, ntiles - first);  // tiles of this CTA (1 or 2); ntiles = ts.total()
-  const int ns = nt * P::NSL;                 // k-slices of this CTA
-  const int k0 = b * S;
-
-  if (tid == 0) {
-    prefetch_tensormap(&tmA);
-    prefetch_tensormap(&tmB);
-    prefetch_tensormap(&tmC);
-#pragma unroll
-    for (int s = 0; s < P::STAGES; ++s) mbar_init(&full[s], 1);
-    mbar_init(cbar, 1);
-    fence_mbar_init();
-    for (int t = 0; t < nt; ++t) {
-      int It, Jt;
-      ts.tile(first + t, It, Jt);
-      tile_ij[2 * t] = It;
-      tile_ij[2 * t + 1] = Jt;
-    }
-  }
-  __syncthreads();
-  wait_prior_grid();
-  if (tid == 0) {
-    s16_pair_issue_c<S>(&tmC, Cs, cbar, tile_ij, 0);
-#pragma unroll
-    for (int g = 0; g < P::STAGES; ++g)
-      if (g < ns) s16_pair_issue<S>(&tmA, &tmB, As, Bs, full, tile_ij, k0, g, g);
-  }
-
-  for (int t = 0; t < nt; ++t) {
-    uint32_t acc[8][4];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) acc[r][m] = 16383u | (16383u << 16);
-    bool timed_out = false;
-    for (int sl = 0; sl < P::NSL; ++sl) {
-      const int g = t * P::NSL + sl;
-      const int st = g % P::STAGES;
-      if (!mbar_wait_bounded(&full[st], (g / P::STAGES) & 1)) timed_out = true;
-      const uint32_t *Bw = reinterpret_cast<const uint32_t *>(Bs + st * P::B_BYTES) + 4 * tx;
-      const uint32_t *Aw = reinterpret_cast<const uint32_t *>(As + st * A_BYTES) + ty * KS;
-#pragma unroll
-      for (int qi = 0; qi < KS / 4; ++qi) {
-        const int q = reverse ? KS / 4 - 1 - qi : qi;
-        uint32_t a[8][4];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const uint4 v = *reinterpret_cast<const uint4 *>(Aw + G * r * KS + ((q ^ (ty & 7)) << 2));
-          a[r][0] = v.x; a[r][1] = v.y; a[r][2] = v.z; a[r][3] = v.w;
-        }
-#pragma unroll
-        for (int ui = 0; ui < 4; ++ui) {
-          const int u = reverse ? 3 - ui : ui;
-          const uint4 bv = *reinterpret_cast<const uint4 *>(Bw + (4 * q + u) * (S / 2));
-          const uint32_t bb[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-          for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int m = 0; m < 4; ++m) acc[r][m] = __viaddmin_s16x2(a[r][u], bb[m], acc[r][m]);
-        }
-      }
-      if (__syncthreads_or(timed_out)) {
-        if (tid == 0) {
-          give_up_and_drain(err, full, g, P::STAGES, ns);
-          mbar_wait_bounded(cbar, t & 1);  // this tile's C copy
-        }
-        return;
-      }
-      if (tid == 0 && g + P::STAGES < ns) s16_pair_issue<S>(&tmA, &tmB, As, Bs, full, tile_ij, k0, g + P::STAGES, st);
-    }
-    // fold in the C tile (rows ty + G r, int16 columns 8 tx .. 8 tx + 7)
-    if (__syncthreads_or(!mbar_wait_bounded(cbar, t & 1))) {  // slices still in flight: the next tile's
-      if (tid == 0) {
-        atomicCAS(err, 0, (int)kDevTimeoutTma);
-        for (int g = (t + 1) * P::NSL; g < (t + 1) * P::NSL + P::STAGES && g < ns; ++g)
-          mbar_wait_bounded(&full[g % P::STAGES], (g / P::STAGES) & 1);
-      }
-      return;
-    }
-    const int64_t I0 = (int64_t)lds_volatile(tile_ij + 2 * t) * S, J0 = (int64_t)lds_volatile(tile_ij + 2 * t + 1) * S;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const uint4 c = *reinterpret_cast<const uint4 *>(Cs + (ty + G * r) * (S * 2) + 16 * tx);
-      const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        if (VIA && via) {  // path bookkeeping: the k-block result against the tile's value
-          const int64_t gi = I0 + ty + G * r, gj = J0 + 8 * tx + 2 * m;
-          if (gi < n && gj < n) note_via(via, via_ld, gi, gj, (int)(int16_t)(acc[r][m] & 0xffffu),
-                                          (int)(int16_t)(cw[m] & 0xffffu), b);
-          if (gi < n && gj + 1 < n) note_via(via, via_ld, gi, gj + 1, (int)(int16_t)(acc[r][m] >> 16),
-                                              (int)(int16_t)(cw[m] >> 16), b);
-        }
-        acc[r][m] = __vmins2(acc[r][m], cw[m]);
-      }
-    }
-    __syncthreads();  // every thread has read Cs: the next tile's C may overwrite it
-    if (tid == 0 && t + 1 < nt) s16_pair_issue_c<S>(&tmC, Cs, cbar, tile_ij, t + 1);
-    const bool full_tile = I0 + S <= n && J0 + S <= n;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int64_t gi = I0 + ty + G * r;
-      const int64_t gj = J0 + 8 * tx;
-      if (full_tile) {
-        *reinterpret_cast<uint4 *>(d + gi * ld + gj) = make_uint4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-      } else {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          if (gi < n && gj + 2 * m < n) d[gi * ld + gj + 2 * m] = (int16_t)(acc[r][m] & 0xffffu);
-          if (gi < n && gj + 2 * m + 1 < n) d[gi * ld + gj + 2 * m + 1] = (int16_t)(acc[r][m] >> 16);
-        }
-      }
-    }
-  }
-}
-
 }  // namespace apsp

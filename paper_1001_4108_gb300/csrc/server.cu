@@ -134,7 +134,7 @@ void fail(Request *r, int rc) {
 // are solved one by one on all SMs rather than one CTA each: the batched
 // kernel pays off when it has many graphs to spread over the SMs.  The
 // choice never changes a result: integer results are exact either way, and
-// fp32 requests take an s = 64 batched shape, whose per-element operations
+// fp32 requests take the s = 64 batched shape, whose per-element operations
 // and stage order are those of the single-graph path at s = 64.
 constexpr int kMinBatch = 8;
 

@@ -108,7 +108,7 @@ def test_batched_padded_leading_dimension():
 def test_autotune_and_table_roundtrip(tmp_path):
     rep = binding.autotune(binding.APSP_I32)
     assert rep["dtype"] == "i32" and len(rep["batched"]) == 5 and len(rep["kblock"]) == 5
-    assert all(0 <= b["best"] < 5 and len(b["ms"]) == 5 for b in rep["batched"])
+    assert all(0 <= b["best"] < 4 and len(b["ms"]) == 4 for b in rep["batched"])
     path = str(tmp_path / "tuning.txt")
     binding.tuning_save(path)
     binding.tuning_load(path)
@@ -140,9 +140,9 @@ def _force_variant(tmp_path, variant, dtypes=("i32", "f32", "i16")):
     return saved
 
 
-@pytest.mark.parametrize("variant", [2, 4])
+@pytest.mark.parametrize("variant", [2])
 def test_fp32_batched_s64_equals_single_graph(tmp_path, variant):
-    """The s = 64 batched shapes run the stages of the single-graph path at
+    """The s = 64 batched shape runs the stages of the single-graph path at
     s = 64 with the same per-element operations, so fp32 results are
     bit-identical to apsp_fw (what lets the server pick either kernel)."""
     saved = _force_variant(tmp_path, variant, ("f32",))
@@ -167,7 +167,7 @@ def test_fp32_batched_s64_equals_single_graph(tmp_path, variant):
         binding.tuning_load(saved)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_each_batched_shape(tmp_path, variant):
     """Every kernel shape, forced through a tuning file for all n buckets,
     gives the oracle's result (graphs of all buckets, ragged and whole tiles)."""
