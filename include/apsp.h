@@ -98,6 +98,17 @@ typedef enum apsp_status {
                                      Same results as the int32 path.  Uses library memory
                                      (n^2 x 2 bytes + int16 panels, per device and stream);
                                      APSP_EINVAL with a caller workspace or apsp_fw_paths. */
+#define APSP_FLAG_ONE_LAUNCH 0x100 /* small matrices (s = 64, 2 to 32 stages): every
+                                     stage in one cooperative launch, the tiles spread
+                                     over the CTAs and ordered by per-tile flags in the
+                                     workspace ((3 R^2 + R) x 4 bytes, R = stages; with a
+                                     smaller caller workspace, or with GENERIC,
+                                     REVERSE_K, NO_LOOKAHEAD, tracing or apsp_fw_paths,
+                                     the multi-launch schedule runs).  Same results.
+                                     Not faster than the default on GB300 (measured:
+                                     n = 1024 fp32 333 vs 266 us); kept for study.  A
+                                     flag wait that runs out (2 s) sets the device
+                                     error word to 2 (apsp_device_error).              */
 #define APSP_FLAG_VALIDATE   0x40 /* before solving, check the input against the value
                                      conventions above (one pass over the matrix, then a
                                      stream synchronize): int32 entries <= 2^29 and

@@ -22,6 +22,7 @@ FLAG_NO_GRAPH, FLAG_GENERIC, FLAG_REVERSE_K, FLAG_NEGCYCLE, FLAG_NO_WORKSPACE = 
 FLAG_NO_LOOKAHEAD = 0x20
 FLAG_VALIDATE = 0x40
 FLAG_NARROW = 0x80
+FLAG_ONE_LAUNCH = 0x100
 EVENTS_PER_STAGE = 5
 INF_I32 = 1 << 29
 INF_I16 = 16383

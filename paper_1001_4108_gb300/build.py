@@ -22,7 +22,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libapsp.so")
 SOURCES = ["api.cu", "fw_i32.cu", "fw_f32.cu", "fw_i16.cu", "ubench.cu", "noalloc.cu", "batched.cu", "tuning.cu", "server.cu",
-           "paths.cu", "selftest.cu", "checks.cu"]
+           "paths.cu", "selftest.cu", "checks.cu", "dataflow.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]

@@ -280,6 +280,16 @@ size_t workspace_bytes_for(int64_t n, int dtype, int S) {
   return bufs * panel_bytes_for(n, dtype, S);
 }
 
+// The workspace a call with `flags` uses: with APSP_FLAG_ONE_LAUNCH on a
+// small matrix, at least the one-launch schedule's per-tile flags.
+size_t workspace_bytes_with(int64_t n, int dtype, int S, int flags) {
+  size_t bytes = workspace_bytes_for(n, dtype, S);
+  const int64_t R = (n + S - 1) / S;
+  if ((flags & APSP_FLAG_ONE_LAUNCH) && S == 64 && R >= kDataflowMinRounds && R <= kDataflowMaxRounds)
+    bytes = std::max(bytes, dataflow_flag_bytes((int)R));
+  return bytes;
+}
+
 // Device buffer of apsp_fw_host, one per device, grown on demand.
 struct HostStage {
   std::mutex mu;
@@ -413,7 +423,7 @@ int solve(void *dist, int64_t n, int64_t ld, int dtype, const apsp_options *opt,
       return APSP_OK;
     }
   }
-  const size_t need = (a.flags & APSP_FLAG_NO_WORKSPACE) ? 0 : workspace_bytes_for(n, dtype, a.S);
+  const size_t need = (a.flags & APSP_FLAG_NO_WORKSPACE) ? 0 : workspace_bytes_with(n, dtype, a.S, a.flags);
   if (need) {
     if (opt && opt->workspace) {
       // one panel buffer is enough (plain schedule); two allow the lookahead

@@ -44,6 +44,15 @@ struct RunArgs {
   bool require_ws;
 };
 
+// One-launch schedule for small matrices (dataflow.cu, APSP_FLAG_ONE_LAUNCH):
+// s = 64 and a stage count in [kDataflowMinRounds, kDataflowMaxRounds].  Its
+// per-tile flags (dataflow_flag_bytes) live at the start of the workspace.
+// run_dataflow returns an apsp_status.
+constexpr int kDataflowMinRounds = 2;
+constexpr int kDataflowMaxRounds = 32;
+size_t dataflow_flag_bytes(int R);
+int run_dataflow(const RunArgs &a, int dtype, int *flags);
+
 // Events a traced solve records per stage (apsp_options.events).
 constexpr int kEventsPerStage = 5;
 // Smallest tile-grid side R for which the lookahead schedule is used.

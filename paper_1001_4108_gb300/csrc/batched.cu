@@ -13,210 +13,11 @@
 #include "../../include/apsp.h"
 #include "apsp_common.cuh"
 #include "apsp_internal.h"
+#include "cta_tile.cuh"
 
 namespace apsp {
 
 namespace {
-
-// Kernel shape: tile side S (= k-block depth inside the CTA) and an M x M
-// register block per thread, (S/M)^2 threads; rows M*ty+a, columns M*tx+c.
-template <int S, int M> struct BShape {
-  static constexpr int Q = S / M;                 // threads per dimension
-  static constexpr int NT = Q * Q;
-  static constexpr int LD = S + 4;                // padded shared-memory row stride
-  static constexpr size_t SMEM = 3 * (size_t)S * LD * 4 + 4 * (size_t)S * 4 + 16;
-  // CTAs per SM the register budget is sized for (s 64: three, as the
-  // shared memory allows; 0 = no bound)
-  static constexpr int MIN_BLOCKS = S == 64 ? 3 : 0;
-};
-
-// Reinterprets a 32-bit word as the compute type (int32 or fp32).
-template <typename C> __device__ __forceinline__ C word_as(int v);
-template <> __device__ __forceinline__ int32_t word_as<int32_t>(int v) { return v; }
-template <> __device__ __forceinline__ float word_as<float>(int v) { return __int_as_float(v); }
-
-// Global <-> register moves of one S x S tile, M x M elements per thread
-// (rows M ty + a, columns M tx + c).  `vec`: 32-bit elements, 16-byte
-// aligned matrix and rows (ld % 4 == 0), so that with M = 4 each row of a
-// thread's block moves as one 128-bit access.
-template <typename T, int S, int M>
-struct TileIO {
-  using C = typename Arith<T>::C;
-  static constexpr int LD = BShape<S, M>::LD;
-  // A tile entirely inside the matrix needs no masks (the common case).
-  static constexpr bool kVec = M == 4 && sizeof(T) == 4;
-  __device__ static void load(const T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, int ty, int tx,
-                              C (&x)[M][M], bool vec) {
-    if (r0 + S <= n && c0 + S <= n) {
-      const T *p = d + (r0 + M * ty) * ld + c0 + M * tx;
-      if constexpr (kVec) {
-        if (vec) {
-#pragma unroll
-          for (int a = 0; a < M; ++a) {
-            const int4 v = *reinterpret_cast<const int4 *>(p + a * ld);
-            x[a][0] = word_as<C>(v.x);
-            x[a][1] = word_as<C>(v.y);
-            x[a][2] = word_as<C>(v.z);
-            x[a][3] = word_as<C>(v.w);
-          }
-          return;
-        }
-      }
-#pragma unroll
-      for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::load(p[a * ld + c]);
-      return;
-    }
-#pragma unroll
-    for (int a = 0; a < M; ++a)
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        const int64_t gi = r0 + M * ty + a, gj = c0 + M * tx + c;
-        x[a][c] = (gi < n && gj < n) ? Arith<T>::load(d[gi * ld + gj]) : Arith<T>::inf();
-      }
-  }
-  __device__ static void store(T *d, int64_t ld, int64_t n, int64_t r0, int64_t c0, int ty, int tx,
-                               const C (&x)[M][M], bool last, bool vec) {
-    if (r0 + S <= n && c0 + S <= n) {
-      T *p = d + (r0 + M * ty) * ld + c0 + M * tx;
-      if constexpr (kVec) {
-        if (vec) {
-#pragma unroll
-          for (int a = 0; a < M; ++a) {
-            C v[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = last ? Arith<T>::finish(x[a][c]) : x[a][c];
-            *reinterpret_cast<int4 *>(p + a * ld) =
-                make_int4(__builtin_bit_cast(int, v[0]), __builtin_bit_cast(int, v[1]),
-                          __builtin_bit_cast(int, v[2]), __builtin_bit_cast(int, v[3]));
-          }
-          return;
-        }
-      }
-#pragma unroll
-      for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int c = 0; c < M; ++c) p[a * ld + c] = last ? Arith<T>::finish(x[a][c]) : (T)x[a][c];
-      return;
-    }
-#pragma unroll
-    for (int a = 0; a < M; ++a)
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        const int64_t gi = r0 + M * ty + a, gj = c0 + M * tx + c;
-        if (gi < n && gj < n) d[gi * ld + gj] = last ? Arith<T>::finish(x[a][c]) : (T)x[a][c];
-      }
-  }
-  __device__ static void to_smem(C *s, int ty, int tx, const C (&x)[M][M]) {
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-      if constexpr (M == 4 && sizeof(C) == 4) {  // 16-byte aligned: padded rows of S + 4 words
-        *reinterpret_cast<int4 *>(s + (M * ty + a) * LD + M * tx) =
-            make_int4(__builtin_bit_cast(int, x[a][0]), __builtin_bit_cast(int, x[a][1]),
-                      __builtin_bit_cast(int, x[a][2]), __builtin_bit_cast(int, x[a][3]));
-      } else {
-#pragma unroll
-        for (int c = 0; c < M; ++c) s[(M * ty + a) * LD + M * tx + c] = x[a][c];
-      }
-    }
-  }
-};
-
-
-// acc[a][c] <- min(acc[a][c], min_k A[M ty + a][k] + B[k][M tx + c]) over the
-// first 4 * kq_end k's of the tile (the k-block's vertices inside the graph,
-// rounded up: the padding k's hold infinity); A and B row-major in shared
-// memory with the padded stride.
-template <typename T, int S, int M>
-__device__ __forceinline__ void minplus_tile(typename Arith<T>::C (&acc)[M][M], const typename Arith<T>::C *A,
-                                             const typename Arith<T>::C *B, int ty, int tx, int kq_end) {
-  using C = typename Arith<T>::C;
-  constexpr int LD = BShape<S, M>::LD;
-  static_assert(sizeof(C) == 4 && (M == 2 || M == 4), "vector shared loads of 4-byte elements");
-  static_assert((LD * 4) % 16 == 0, "16-byte aligned rows");
-#pragma unroll 4
-  for (int kq = 0; kq < kq_end; ++kq) {
-    C av[M][4];
-#pragma unroll
-    for (int a = 0; a < M; ++a) {  // 4 k's of row M ty + a: one 128-bit load
-      const int4 v = *reinterpret_cast<const int4 *>(A + (M * ty + a) * LD + 4 * kq);
-      av[a][0] = word_as<C>(v.x);
-      av[a][1] = word_as<C>(v.y);
-      av[a][2] = word_as<C>(v.z);
-      av[a][3] = word_as<C>(v.w);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const C *q = B + (4 * kq + u) * LD + M * tx;
-      C bv[M];
-      if constexpr (M == 4) {
-        const int4 v = *reinterpret_cast<const int4 *>(q);
-        bv[0] = word_as<C>(v.x);
-        bv[1] = word_as<C>(v.y);
-        bv[2] = word_as<C>(v.z);
-        bv[3] = word_as<C>(v.w);
-      } else {
-        const int2 v = *reinterpret_cast<const int2 *>(q);
-        bv[0] = word_as<C>(v.x);
-        bv[1] = word_as<C>(v.y);
-      }
-#pragma unroll
-      for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int c = 0; c < M; ++c) acc[a][c] = Arith<T>::relax(acc[a][c], av[a][u], bv[c]);
-    }
-  }
-}
-
-// Phase 1 inside one CTA: closes the diagonal tile (p0, p0) -- kvalid
-// sequential k steps on an M x M register block per thread, row and column
-// k + 1 published through a double buffer (one barrier per step) -- stores it
-// (clamped in the last stage) and leaves it in Ds (padded rows).  Ends with a
-// barrier.
-template <typename T, int S, int M>
-__device__ __forceinline__ void close_diag(T *d, int64_t ld, int64_t n, int64_t p0, int kvalid, bool last,
-                                           bool vec, typename Arith<T>::C *Ds, typename Arith<T>::C *rowbuf,
-                                           typename Arith<T>::C *colbuf, int ty, int tx) {
-  using C = typename Arith<T>::C;
-  using IO = TileIO<T, S, M>;
-  C x[M][M];
-  IO::load(d, ld, n, p0, p0, ty, tx, x, vec);
-  if (ty == 0)
-#pragma unroll
-    for (int c = 0; c < M; ++c) rowbuf[M * tx + c] = x[0][c];
-  if (tx == 0)
-#pragma unroll
-    for (int a = 0; a < M; ++a) colbuf[M * ty + a] = x[a][0];
-  for (int kq = 0; kq < (kvalid + M - 1) / M; ++kq) {
-#pragma unroll
-    for (int u = 0; u < M; ++u) {
-      const int k = M * kq + u;
-      __syncthreads();
-      C rk[M], ck[M];
-#pragma unroll
-      for (int c = 0; c < M; ++c) rk[c] = rowbuf[(k & 1) * S + M * tx + c];
-#pragma unroll
-      for (int a = 0; a < M; ++a) ck[a] = colbuf[(k & 1) * S + M * ty + a];
-#pragma unroll
-      for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::relax(x[a][c], ck[a], rk[c]);
-      const int k1 = k + 1;
-      if (k1 < S) {
-        if (ty == k1 / M)
-#pragma unroll
-          for (int c = 0; c < M; ++c) rowbuf[(k1 & 1) * S + M * tx + c] = x[(u + 1) % M][c];
-        if (tx == k1 / M)
-#pragma unroll
-          for (int a = 0; a < M; ++a) colbuf[(k1 & 1) * S + M * ty + a] = x[a][(u + 1) % M];
-      }
-    }
-  }
-  IO::store(d, ld, n, p0, p0, ty, tx, x, last, vec);
-  IO::to_smem(Ds, ty, tx, x);
-  __syncthreads();
-}
 
 template <typename T, int S, int M>
 __global__ void __launch_bounds__(BShape<S, M>::NT, BShape<S, M>::MIN_BLOCKS)
@@ -230,9 +31,9 @@ __global__ void __launch_bounds__(BShape<S, M>::NT, BShape<S, M>::MIN_BLOCKS)
   C *Ds = reinterpret_cast<C *>(smem_raw);  // closed diagonal tile
   C *Ps = Ds + S * LD;                      // first operand tile
   C *Qs = Ps + S * LD;                      // second operand tile
-  C *rowbuf = Qs + S * LD;                  // [2][S]
-  C *colbuf = rowbuf + 2 * S;               // [2][S]
-  int *s_g = reinterpret_cast<int *>(colbuf + 2 * S);
+  C *rowbuf = Qs + S * LD;                  // [2][2][S]
+  C *colbuf = rowbuf + 4 * S;               // [2][2][S]
+  int *s_g = reinterpret_cast<int *>(colbuf + 4 * S);
   const int tx = threadIdx.x % Q, ty = threadIdx.x / Q;
 
   while (true) {

@@ -197,6 +197,17 @@ static int run_rounds(const RunArgs &a) {
   const bool ragged = (n % S) != 0;
   const int reverse = (a.flags & APSP_FLAG_REVERSE_K) ? 1 : 0;
   const bool generic_only = (a.flags & APSP_FLAG_GENERIC) != 0;
+
+  // Small matrices, on request: all stages in one launch (same values as below).
+  if constexpr (S == 64) {
+    constexpr int kFlagsOff = APSP_FLAG_GENERIC | APSP_FLAG_REVERSE_K | APSP_FLAG_NO_LOOKAHEAD;
+    if ((a.flags & APSP_FLAG_ONE_LAUNCH) && R >= kDataflowMinRounds && R <= kDataflowMaxRounds &&
+        !(a.flags & kFlagsOff) && !a.via && !a.events && !a.first_src && !a.last_dst && a.ws &&
+        a.ws_bytes >= dataflow_flag_bytes(R) && reinterpret_cast<uintptr_t>(a.ws) % 16 == 0) {
+      const int dt = std::is_same<T, float>::value ? APSP_F32 : std::is_same<T, int16_t>::value ? APSP_I16 : APSP_I32;
+      return run_dataflow(a, dt, static_cast<int *>(a.ws));
+    }
+  }
   const cudaStream_t st = a.stream;
   const int64_t np = (int64_t)R * S;
 

@@ -223,6 +223,65 @@ def test_lookahead_equals_plain(dt, n, kb):
         np.testing.assert_array_equal(a, _oracle(dt, w))
 
 
+@pytest.mark.parametrize("dt", ["f32", "i32", "i16"])
+@pytest.mark.parametrize("n", [65, 128, 129, 300, 640, 1000, 1024, 1500, 2047, 2048])
+def test_one_launch_equals_multi_launch(dt, n):
+    """APSP_FLAG_ONE_LAUNCH: every stage in one cooperative launch (tiles
+    spread over the CTAs, ordered by per-tile flags).  Bit-identical to the
+    multi-launch schedules, and to the oracle for the integers.  Stage counts
+    2 to 32, whole and ragged; direct, library graph and a user's capture."""
+    w = _graph(dt, n, seed=n + 7)
+    cfg = binding.query_config(n, binding.dtype_code(w.dtype))
+    assert cfg.kblock == 64 and 2 <= cfg.rounds <= 32
+    F = binding.FLAG_ONE_LAUNCH
+    one = gpu_solve(w, flags=F | binding.FLAG_NO_GRAPH)
+    multi = gpu_solve(w)
+    plain = gpu_solve(w, flags=binding.FLAG_NO_LOOKAHEAD)
+    assert np.array_equal(one, multi) and np.array_equal(one, plain)
+    if dt == "f32":
+        if n <= 1024:
+            assert_fp32_close(one, oracle.fw_f64(w))
+    else:
+        np.testing.assert_array_equal(one, _oracle(dt, w))
+    src = torch.from_numpy(w).cuda()
+    t = torch.empty_like(src)
+    for _ in range(3):  # direct, captured graph, replay
+        t.copy_(src)
+        binding.apsp_fw(t, flags=F)
+        torch.cuda.synchronize()
+        assert np.array_equal(t.cpu().numpy(), one)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        binding.apsp_fw(t, stream=s, flags=F)
+    t.copy_(src)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(t.cpu().numpy(), one)
+    assert binding.device_error() == 0
+
+
+def test_one_launch_workspace_and_limits():
+    # a caller workspace too small for the flags, or a size outside 2..32
+    # stages: the multi-launch schedule runs, same result
+    F = binding.FLAG_ONE_LAUNCH
+    w = inputs.c1(seed=3, n=1000)
+    ref = gpu_solve(w)
+    np.testing.assert_array_equal(ref, oracle.fw_int32_conv(w))
+    need = (3 * 16 * 16 + 16) * 4  # 16 stages
+    for size in (need, need - 4):
+        ws = torch.zeros(size // 4 + 1, dtype=torch.int32, device="cuda")
+        t = torch.from_numpy(w).cuda()
+        opt = binding.Options(0, F, None, 0, ws.data_ptr(), size)
+        assert binding.apsp_fw_raw(t.data_ptr(), 1000, 1000, binding.APSP_I32,
+                                   torch.cuda.current_stream().cuda_stream, opt) == binding.APSP_OK
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(t.cpu().numpy(), ref)
+    for n in (40, 2100):  # 1 stage, 33 stages
+        x = inputs.int_graph(n, 0.05, 1, 1000, seed=n)
+        np.testing.assert_array_equal(gpu_solve(x, flags=F), gpu_solve(x))
+
+
 def test_lookahead_graph_replay_and_user_capture():
     n = 1100
     w = _graph("i32", n, seed=3)
