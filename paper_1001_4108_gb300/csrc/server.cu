@@ -233,9 +233,32 @@ void scheduler(Server *s) {
   }
 }
 
+// Row-by-row copy between host matrices of different leading dimensions.
+// Large matrices are split into row ranges copied by several host threads: a
+// single core moves a 64 MiB matrix in several milliseconds, which would
+// stall the submitting (or collecting) thread and every request behind it.
 void copy_rows(void *dst, int64_t dld, const void *src, int64_t sld, int64_t n, int es) {
-  for (int64_t i = 0; i < n; ++i)
-    memcpy(static_cast<char *>(dst) + i * dld * es, static_cast<const char *>(src) + i * sld * es, (size_t)n * es);
+  auto range = [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i)
+      memcpy(static_cast<char *>(dst) + i * dld * es, static_cast<const char *>(src) + i * sld * es,
+             (size_t)n * es);
+  };
+  constexpr size_t kParallelBytes = 4u << 20;
+  const size_t bytes = (size_t)n * n * es;
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int parts = bytes < kParallelBytes ? 1 : std::max(1, std::min(8, hw / 2));
+  if (parts <= 1) {
+    range(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  const int64_t per = (n + parts - 1) / parts;
+  for (int p = 1; p < parts; ++p) {
+    const int64_t i0 = p * per, i1 = std::min<int64_t>(n, i0 + per);
+    if (i0 < i1) th.emplace_back(range, i0, i1);
+  }
+  range(0, std::min<int64_t>(n, per));
+  for (auto &t : th) t.join();
 }
 
 // Delivers a finished request (s->mu held); frees it.
