@@ -25,7 +25,6 @@ __global__ void __launch_bounds__(BShape<S, M>::NT, BShape<S, M>::MIN_BLOCKS)
                                                                    int *counter) {
   using C = typename Arith<T>::C;
   using IO = TileIO<T, S, M>;
-  constexpr int Q = BShape<S, M>::Q;
   constexpr int LD = BShape<S, M>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *Ds = reinterpret_cast<C *>(smem_raw);  // closed diagonal tile
@@ -34,7 +33,8 @@ __global__ void __launch_bounds__(BShape<S, M>::NT, BShape<S, M>::MIN_BLOCKS)
   C *rowbuf = Qs + S * LD;                  // [2][2][S]
   C *colbuf = rowbuf + 4 * S;               // [2][2][S]
   int *s_g = reinterpret_cast<int *>(colbuf + 4 * S);
-  const int tx = threadIdx.x % Q, ty = threadIdx.x / Q;
+  int ty, tx;
+  block_of_thread<S, M>(threadIdx.x, ty, tx);
 
   while (true) {
     if (threadIdx.x == 0) *s_g = atomicAdd(counter, 1);
@@ -63,10 +63,12 @@ __global__ void __launch_bounds__(BShape<S, M>::NT, BShape<S, M>::MIN_BLOCKS)
         IO::load(d, ld, n, r0, c0, ty, tx, acc, vec);
         IO::to_smem(Ps, ty, tx, acc);
         __syncthreads();
-        if (row)
-          minplus_tile<T, S, M>(acc, Ds, Ps, ty, tx, kq_end);
-        else
-          minplus_tile<T, S, M>(acc, Ps, Ds, ty, tx, kq_end);
+        if (warp_has_work<M>(ty, tx, (int)min((int64_t)S, n - r0), (int)min((int64_t)S, n - c0))) {
+          if (row)
+            minplus_tile<T, S, M>(acc, Ds, Ps, ty, tx, kq_end);
+          else
+            minplus_tile<T, S, M>(acc, Ps, Ds, ty, tx, kq_end);
+        }
         IO::store(d, ld, n, r0, c0, ty, tx, acc, last, vec);
         __syncthreads();
       }
@@ -83,7 +85,8 @@ __global__ void __launch_bounds__(BShape<S, M>::NT, BShape<S, M>::MIN_BLOCKS)
           IO::load(d, ld, n, r0, c0, ty, tx, acc, vec);
           IO::to_smem(Qs, ty, tx, bt);
           __syncthreads();
-          minplus_tile<T, S, M>(acc, Ps, Qs, ty, tx, kq_end);
+          if (warp_has_work<M>(ty, tx, (int)min((int64_t)S, n - r0), (int)min((int64_t)S, n - c0)))
+            minplus_tile<T, S, M>(acc, Ps, Qs, ty, tx, kq_end);
           IO::store(d, ld, n, r0, c0, ty, tx, acc, last, vec);
           __syncthreads();
         }

@@ -23,6 +23,27 @@ template <int S, int M> struct BShape {
   static constexpr int MIN_BLOCKS = S == 64 ? 3 : 0;
 };
 
+// Thread -> block of a tile: each warp covers 4 block rows x 8 block columns
+// (4M rows x 8M columns of the tile), so that the warps whose rows or columns
+// all lie outside the matrix can skip their arithmetic as a whole (an idle
+// lane inside a working warp saves nothing).  Needs (S/M) % 8 == 0.
+template <int S, int M>
+__device__ __forceinline__ void block_of_thread(int t, int &ty, int &tx) {
+  constexpr int Q = S / M;
+  static_assert(Q % 8 == 0 && (Q * Q) % 32 == 0, "whole warps of 4 x 8 blocks");
+  constexpr int WC = Q / 8;  // warps across the tile
+  const int w = t / 32, l = t % 32;
+  ty = 4 * (w / WC) + l / 8;
+  tx = 8 * (w % WC) + l % 8;
+}
+
+// Whether the warp holding block (ty, tx) has any element with row < rows
+// and column < cols (uniform over the warp).
+template <int M>
+__device__ __forceinline__ bool warp_has_work(int ty, int tx, int rows, int cols) {
+  return __any_sync(0xffffffffu, M * ty < rows && M * tx < cols);
+}
+
 // Reinterprets a 32-bit word as the compute type (int32 or fp32).
 template <typename C> __device__ __forceinline__ C word_as(int v);
 template <> __device__ __forceinline__ int32_t word_as<int32_t>(int v) { return v; }
@@ -206,41 +227,49 @@ __device__ __forceinline__ void close_diag(T *d, int64_t ld, int64_t n, int64_t 
       colbuf[S + M * ty + a] = x[a][1];
     }
   }
+  // Warps whose rows or columns all lie beyond the k-block's vertices hold
+  // padding only (never stored): they skip the arithmetic and keep the
+  // infinity they loaded, which they still publish when they own a pivot
+  // row or column -- every value that reaches a real entry is then a real
+  // distance or a sum involving infinity, as without the skip.
+  const bool work = warp_has_work<M>(ty, tx, kvalid, kvalid);
   for (int kq = 0; kq < (kvalid + M - 1) / M; ++kq) {
 #pragma unroll
     for (int h = 0; h < M / 2; ++h) {
       const int g = kq * (M / 2) + h;  // pair of steps k0, k0 + 1
       const int k0 = 2 * g;
       __syncthreads();
-      const C *rb = rowbuf + (g & 1) * 2 * S;
-      const C *cb = colbuf + (g & 1) * 2 * S;
-      C r0[M], r1[M], c0[M], c1[M];
+      if (work) {
+        const C *rb = rowbuf + (g & 1) * 2 * S;
+        const C *cb = colbuf + (g & 1) * 2 * S;
+        C r0[M], r1[M], c0[M], c1[M];
 #pragma unroll
-      for (int c = 0; c < M; ++c) {
-        r0[c] = rb[M * tx + c];
-        r1[c] = rb[S + M * tx + c];
+        for (int c = 0; c < M; ++c) {
+          r0[c] = rb[M * tx + c];
+          r1[c] = rb[S + M * tx + c];
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          c0[a] = cb[M * ty + a];
+          c1[a] = cb[S + M * ty + a];
+        }
+        const C p10 = rb[S + k0];  // x[k0+1][k0]
+        const C p01 = rb[k0 + 1];  // x[k0][k0+1]
+        // step k0
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+          for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::relax(x[a][c], c0[a], r0[c]);
+#pragma unroll
+        for (int c = 0; c < M; ++c) r1[c] = Arith<T>::relax(r1[c], p10, r0[c]);
+#pragma unroll
+        for (int a = 0; a < M; ++a) c1[a] = Arith<T>::relax(c1[a], c0[a], p01);
+        // step k0 + 1
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+          for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::relax(x[a][c], c1[a], r1[c]);
       }
-#pragma unroll
-      for (int a = 0; a < M; ++a) {
-        c0[a] = cb[M * ty + a];
-        c1[a] = cb[S + M * ty + a];
-      }
-      const C p10 = rb[S + k0];  // x[k0+1][k0]
-      const C p01 = rb[k0 + 1];  // x[k0][k0+1]
-      // step k0
-#pragma unroll
-      for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::relax(x[a][c], c0[a], r0[c]);
-#pragma unroll
-      for (int c = 0; c < M; ++c) r1[c] = Arith<T>::relax(r1[c], p10, r0[c]);
-#pragma unroll
-      for (int a = 0; a < M; ++a) c1[a] = Arith<T>::relax(c1[a], c0[a], p01);
-      // step k0 + 1
-#pragma unroll
-      for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int c = 0; c < M; ++c) x[a][c] = Arith<T>::relax(x[a][c], c1[a], r1[c]);
       // publish rows and columns k0 + 2, k0 + 3 (local rows lr, lr + 1 of
       // their owners) for the next pair
       const int k2 = k0 + 2;

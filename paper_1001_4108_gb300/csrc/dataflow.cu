@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(DShape::NT, 2)
   __shared__ __align__(16) C colbuf[4 * S];
   __shared__ int s_ok;
   const int tid = threadIdx.x;
-  const int tx = tid % DShape::Q, ty = tid / DShape::Q;
+  int ty, tx;
+  block_of_thread<kDS, kDM>(tid, ty, tx);
   int *ver = flags;             // [R * R]
   int *rd_row = ver + R * R;    // [R * R], index b * R + J
   int *rd_col = rd_row + R * R; // [R * R], index b * R + I
@@ -155,10 +156,12 @@ __global__ void __launch_bounds__(DShape::NT, 2)
           IO::to_smem(As, ty, tx, x);
           IO::to_smem(Bs, ty, tx, acc);
           __syncthreads();
-          if (I == s)
-            minplus_tile<T, S, M>(acc, As, Bs, ty, tx, kq_end);  // row panel: D (x) X
-          else
-            minplus_tile<T, S, M>(acc, Bs, As, ty, tx, kq_end);  // column panel: X (x) D
+          if (warp_has_work<M>(ty, tx, (int)min((int64_t)S, n - r0), (int)min((int64_t)S, n - c0))) {
+            if (I == s)
+              minplus_tile<T, S, M>(acc, As, Bs, ty, tx, kq_end);  // row panel: D (x) X
+            else
+              minplus_tile<T, S, M>(acc, Bs, As, ty, tx, kq_end);  // column panel: X (x) D
+          }
           IO::store(d, ld, n, r0, c0, ty, tx, acc, last, vec);
         } else {
           C a[M][M], bt[M][M], acc[M][M];
@@ -168,7 +171,8 @@ __global__ void __launch_bounds__(DShape::NT, 2)
           IO::to_smem(As, ty, tx, a);
           IO::to_smem(Bs, ty, tx, bt);
           __syncthreads();
-          minplus_tile<T, S, M>(acc, As, Bs, ty, tx, kq_end);
+          if (warp_has_work<M>(ty, tx, (int)min((int64_t)S, n - r0), (int)min((int64_t)S, n - c0)))
+            minplus_tile<T, S, M>(acc, As, Bs, ty, tx, kq_end);
           IO::store(d, ld, n, r0, c0, ty, tx, acc, last, vec);
         }
         __syncthreads();  // the tile is stored and its operands read
