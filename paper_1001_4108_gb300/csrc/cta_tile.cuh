@@ -8,6 +8,10 @@
 
 #include "apsp_common.cuh"
 
+#ifndef APSP_BATCH64_CTAS
+#define APSP_BATCH64_CTAS 3
+#endif
+
 namespace apsp {
 
 // Kernel shape: tile side S (= k-block depth inside the CTA) and an M x M
@@ -18,9 +22,9 @@ template <int S, int M> struct BShape {
   static constexpr int LD = S + 4;                // padded shared-memory row stride
   // three tiles, the phase-1 row and column buffers (4 S words each), a slot
   static constexpr size_t SMEM = 3 * (size_t)S * LD * 4 + 8 * (size_t)S * 4 + 16;
-  // CTAs per SM the register budget is sized for (s 64: three, as the
-  // shared memory allows; 0 = no bound)
-  static constexpr int MIN_BLOCKS = S == 64 ? 3 : 0;
+  // CTAs per SM the register budget is sized for (s 64: APSP_BATCH64_CTAS,
+  // which the shared memory allows; 0 = no bound)
+  static constexpr int MIN_BLOCKS = S == 64 ? APSP_BATCH64_CTAS : 0;
 };
 
 // Thread -> block of a tile: each warp covers 4 block rows x 8 block columns
