@@ -336,16 +336,18 @@ typedef struct apsp_stats {
 /* Creates a server (its scheduler thread, streams and workspaces). */
 APSP_API int apsp_server_create(apsp_server **out, const apsp_server_config *cfg);
 
-/* Queues one request; the matrix (host memory, row-major, leading dimension
-   ld >= n) is copied before the call returns.  *ticket identifies it.
-   APSP_ENOMEM if the matrix alone exceeds the HBM budget, APSP_EUNSUPPORTED
-   if n > max_n, APSP_EBUSY if the server is shutting down. */
+/* Queues one request; the matrix (host or device memory, row-major, leading
+   dimension ld >= n) is copied before the call returns.  *ticket identifies
+   it.  APSP_ENOMEM if the matrix alone exceeds the HBM budget,
+   APSP_EUNSUPPORTED if n > max_n, APSP_EBUSY if the server is shutting down,
+   APSP_ECUDA if copying from device memory fails. */
 APSP_API int apsp_submit(apsp_server *srv, const void *host_dist, int64_t n, int64_t ld, int dtype, int flags,
                          uint64_t *ticket);
 
 /* APSP_EPENDING while the request runs; otherwise delivers the distances
-   into out_dist (host, leading dimension out_ld >= n; NULL = discard) and
-   retires the ticket, returning APSP_OK or the request's error. */
+   into out_dist (host or device memory, leading dimension out_ld >= n;
+   NULL = discard) and retires the ticket, returning APSP_OK or the request's
+   error. */
 APSP_API int apsp_poll(apsp_server *srv, uint64_t ticket, void *out_dist, int64_t out_ld);
 
 /* apsp_poll that blocks up to timeout_us microseconds (< 0: no limit);

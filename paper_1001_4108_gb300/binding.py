@@ -310,43 +310,52 @@ class Server:
         self._shapes = {}
 
     def submit(self, a) -> int:
-        """Queue a numpy matrix (copied before return); returns the ticket."""
+        """Queue a matrix -- a numpy array or a (CUDA or CPU) torch tensor,
+        copied before return; returns the ticket."""
         import numpy as np
-        assert isinstance(a, np.ndarray) and a.ndim == 2
         t = ctypes.c_uint64()
         n = a.shape[0]
-        if n:
-            assert a.strides[1] == a.itemsize, "row-major matrix with unit column stride expected"
-        ld = a.strides[0] // a.itemsize if n else 0
-        _check(lib().apsp_submit(self._h, a.ctypes.data, n, ld, dtype_code(a.dtype), 0, ctypes.byref(t)),
-               "apsp_submit")
-        self._shapes[t.value] = (n, a.dtype)
+        if isinstance(a, np.ndarray):
+            assert a.ndim == 2
+            if n:
+                assert a.strides[1] == a.itemsize, "row-major matrix with unit column stride expected"
+            ptr, ld, dt = a.ctypes.data, (a.strides[0] // a.itemsize if n else 0), a.dtype
+        else:
+            assert a.dim() == 2 and (n == 0 or a.stride(1) == 1), "row-major matrix expected"
+            ptr, ld, dt = a.data_ptr(), (a.stride(0) if n else 0), a.dtype
+        _check(lib().apsp_submit(self._h, ptr, n, ld, dtype_code(dt), 0, ctypes.byref(t)), "apsp_submit")
+        self._shapes[t.value] = (n, np.dtype(str(dt).split(".")[-1]))
         return t.value
 
-    def _out(self, ticket):
+    def _out(self, ticket, out):
         import numpy as np
+        if out is not None:
+            assert out.dim() == 2 and out.stride(1) == 1
+            return out, out.data_ptr(), out.stride(0)
         n, dt = self._shapes[ticket]
-        return np.empty((n, n), dtype=dt)
+        a = np.empty((n, n), dtype=dt)
+        return a, a.ctypes.data, n
 
-    def poll(self, ticket: int):
-        """The result (numpy) if finished, else None."""
-        out = self._out(ticket)
-        st = lib().apsp_poll(self._h, ticket, out.ctypes.data, out.shape[0])
+    def poll(self, ticket: int, out=None):
+        """The result if finished, else None: a new numpy array, or `out` (a
+        torch tensor in host or device memory) filled in place."""
+        res, ptr, ld = self._out(ticket, out)
+        st = lib().apsp_poll(self._h, ticket, ptr, ld)
         if st == APSP_EPENDING:
             return None
         self._shapes.pop(ticket, None)
         _check(st, "apsp_poll")
-        return out
+        return res
 
-    def wait(self, ticket: int, timeout_s: float | None = None):
-        out = self._out(ticket)
+    def wait(self, ticket: int, timeout_s: float | None = None, out=None):
+        res, ptr, ld = self._out(ticket, out)
         us = -1 if timeout_s is None else int(timeout_s * 1e6)
-        st = lib().apsp_wait(self._h, ticket, out.ctypes.data, out.shape[0], us)
+        st = lib().apsp_wait(self._h, ticket, ptr, ld, us)
         if st == APSP_ETIMEOUT:
             return None
         self._shapes.pop(ticket, None)
         _check(st, "apsp_wait")
-        return out
+        return res
 
     def stats(self, reset: bool = False) -> dict:
         s = Stats()

@@ -1,8 +1,9 @@
 // Serving form: a request loop that solves APSP requests of different sizes
 // and element types as they arrive (continuous batching).
 //
-//   submit  copies the caller's host matrix into pinned staging memory and
-//           queues the request (the caller keeps ownership of its buffer);
+//   submit  copies the caller's matrix (host or device memory) into pinned
+//           staging memory and queues the request (the caller keeps
+//           ownership of its buffer);
 //   the scheduler thread admits queued requests, oldest first, while an
 //           in-flight slot is free and the request's device footprint fits the
 //           HBM budget; each admitted request is uploaded once and solved on
@@ -13,7 +14,8 @@
 //           the result is copied back to pinned memory, the device buffer is
 //           released in stream order, and a host callback marks completion
 //           (latency = submit -> result in host memory);
-//   poll / wait deliver the result into the caller's buffer.
+//   poll / wait deliver the result into the caller's buffer (host or device
+//           memory).
 // A request's result is the same whether it is solved alone or in a mix:
 // integer results are exact, and fp32 requests get the same per-element
 // operations in the same stage order (s = 64 up to n = 512) from the batched
@@ -261,10 +263,34 @@ void copy_rows(void *dst, int64_t dld, const void *src, int64_t sld, int64_t n, 
   for (auto &t : th) t.join();
 }
 
+// Whether p is device memory of some GPU (not host, pinned or not).
+bool on_device(const void *p) {
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+    cudaGetLastError();  // an unregistered host pointer on older runtimes
+    return false;
+  }
+  return pa.type == cudaMemoryTypeDevice;
+}
+
+// Copies an n x n matrix between a caller's buffer and a pinned staging
+// buffer; the caller's side may be host or device memory.
+int copy_matrix(void *dst, int64_t dld, const void *src, int64_t sld, int64_t n, int es, bool device_side) {
+  if (!device_side) {
+    copy_rows(dst, dld, src, sld, n, es);
+    return APSP_OK;
+  }
+  return cudaMemcpy2D(dst, (size_t)dld * es, src, (size_t)sld * es, (size_t)n * es, (size_t)n, cudaMemcpyDefault) ==
+                 cudaSuccess
+             ? APSP_OK
+             : APSP_ECUDA;
+}
+
 // Delivers a finished request (s->mu held); frees it.
 int deliver(Server *s, Request *r, void *out, int64_t out_ld) {
   int rc = r->state.load() == kDone ? APSP_OK : r->status;
-  if (rc == APSP_OK && out) copy_rows(out, out_ld, r->host, r->ld, r->n, esize(r->dtype));
+  if (rc == APSP_OK && out && r->n > 0)
+    rc = copy_matrix(out, out_ld, r->host, r->ld, r->n, esize(r->dtype), on_device(out));
   if (r->host) s->pinned_free.emplace(r->host_cap, r->host);
   s->table.erase(r->id);
   delete r;
@@ -347,7 +373,12 @@ extern "C" int apsp_submit(apsp_server *h, const void *host_dist, int64_t n, int
     delete r;
     return APSP_ENOMEM;
   }
-  if (n > 0) copy_rows(r->host, r->ld, host_dist, ld, n, esize(dtype));
+  if (n > 0 && copy_matrix(r->host, r->ld, host_dist, ld, n, esize(dtype), on_device(host_dist)) != APSP_OK) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->pinned_free.emplace(r->host_cap, r->host);
+    delete r;
+    return APSP_ECUDA;
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) {

@@ -380,6 +380,7 @@ def test_validate_flag():
         codes.append(binding.apsp_fw_raw(t.data_ptr(), 1024, 1024, binding.APSP_I32, s.cuda_stream, opt))
         opt = binding.Options(0, binding.FLAG_NEGCYCLE, None, 0, None, 0)
         codes.append(binding.apsp_fw_raw(t.data_ptr(), 1024, 1024, binding.APSP_I32, s.cuda_stream, opt))
+        t.add_(0)  # the refused calls enqueue nothing: keep the captured graph non-empty
     assert codes == [binding.APSP_EINVAL, binding.APSP_EINVAL]
 
 

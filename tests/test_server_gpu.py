@@ -99,3 +99,24 @@ def test_poll_pending_and_wait_timeout():
         assert srv.wait(t2) is not None
         # empty matrix completes at once
         assert srv.wait(srv.submit(np.zeros((0, 0), np.int32))).shape == (0, 0)
+
+
+def test_device_matrices_in_and_out():
+    # a request may come from device memory and be delivered into device
+    # memory (or host memory); same values as a solve in place
+    reqs = [inputs.c1(seed=2, n=300), inputs.dense_f32(700, seed=3), inputs.int_graph(1500, 0.05, 1, 100, seed=4)]
+    with binding.Server(max_inflight=8) as srv:
+        for w in reqs:
+            src = torch.from_numpy(w).cuda()
+            ref = src.clone()
+            binding.apsp_fw(ref)
+            t = srv.submit(src)
+            src.fill_(0)  # the server copied it before submit returned
+            out = torch.empty_like(ref)
+            assert srv.wait(t, out=out) is out
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref)
+            t2 = srv.submit(ref.cpu())  # a host tensor, delivered into a host tensor
+            out_h = torch.empty(ref.shape, dtype=ref.dtype)
+            srv.wait(t2, out=out_h)
+            assert torch.equal(out_h, ref.cpu())
