@@ -99,14 +99,14 @@ __global__ void __launch_bounds__(BShape<S, M>::NT, BShape<S, M>::MIN_BLOCKS)
 template <typename T, int S, int M>
 int launch_batched_kernel(const BatchDesc *descs, int count, int *counter, cudaStream_t st) {
   using B = BShape<S, M>;
-  static thread_local int setup_mask = 0;
+  static thread_local uint64_t setup_mask = 0;  // bit per device
   int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return APSP_ECUDA;
-  if (!(setup_mask & (1 << (dev & 31)))) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return APSP_ECUDA;
+  if (!(setup_mask & (1ull << dev))) {
     if (cudaFuncSetAttribute(fw_batched_cta<T, S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM) !=
         cudaSuccess)
       return APSP_ECUDA;
-    setup_mask |= 1 << (dev & 31);
+    setup_mask |= 1ull << dev;
   }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return APSP_ECUDA;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batched_cta<T, S, M>, B::NT, B::SMEM) !=
