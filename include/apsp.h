@@ -393,7 +393,9 @@ APSP_API int apsp_selftest_wait(int64_t limit_ns, void *stream);
  *          4 fp32 packed add.f32x2 + three-input min (two k's per pair),
  *          5 int32 two adds + three-input DPX min (two k's),
  *          6 fp32 two scalar adds + three-input min (two k's),
- *          7 fp32 forms 4 and 6 alternating by column.
+ *          7 fp32 forms 4 and 6 alternating by column,
+ *          8 int32 additions three quarters as multiply-adds by a runtime 1
+ *            (FMA pipe), one quarter as adds, + three-input DPX min.
  *   iters  sweeps of the slice.
  *   blocks blocks to launch (<= 0: 2 per SM); threads must be 256.
  *   sink   device buffer of blocks*256 4-byte words (results are written so

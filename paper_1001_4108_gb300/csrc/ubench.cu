@@ -105,6 +105,9 @@ __global__ void __launch_bounds__(256, 2) ubench_kstep(int64_t iters, T *sink) {
 // form 5: int32, two adds + one three-input minimum per (row, column, k-pair).
 // form 6: fp32, two scalar adds + one three-input minimum per (row, column,
 // k-pair) (the adds may issue on either FMA sub-pipe).
+// form 8: int32, additions split between the pipes -- three of every four as
+// a multiply-add by a runtime 1 (FMA pipe), one as an add (ALU) -- and one
+// three-input DPX minimum per (row, column, k-pair).
 // form 7: fp32, the two forms alternating by column: one packed add for
 // column 2m, two scalar adds for column 2m + 1.
 template <int FORM>
@@ -119,6 +122,7 @@ __global__ void __launch_bounds__(256, 2) ubench_kpair(int64_t iters, void *sink
   const float *B = Bs + 4 * tx;
   float acc[8][8];
   int32_t iacc[8][8];
+  const int32_t one = iters > 0 ? 1 : 0;  // a 1 the compiler cannot fold away
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -161,6 +165,14 @@ __global__ void __launch_bounds__(256, 2) ubench_kpair(int64_t iters, void *sink
             acc[r][2 * m] = min3f(acc[r][2 * m], s0.x, s0.y);
             acc[r][2 * m + 1] =
                 min3f(acc[r][2 * m + 1], __fadd_rn(ap[r].x, bq[m].z), __fadd_rn(ap[r].y, bq[m].w));
+          } else if constexpr (FORM == 8) {
+            const int32_t a0 = __float_as_int(ap[r].x), a1 = __float_as_int(ap[r].y);
+            int32_t s0, s1, s2;
+            asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(s0) : "r"(a0), "r"(one), "r"(__float_as_int(bq[m].x)));
+            asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(s1) : "r"(a1), "r"(one), "r"(__float_as_int(bq[m].y)));
+            asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(s2) : "r"(a0), "r"(one), "r"(__float_as_int(bq[m].z)));
+            iacc[r][2 * m] = __vimin3_s32(iacc[r][2 * m], s0, s1);
+            iacc[r][2 * m + 1] = __vimin3_s32(iacc[r][2 * m + 1], s2, a1 + __float_as_int(bq[m].w));
           } else {
             const int32_t a0 = __float_as_int(ap[r].x), a1 = __float_as_int(ap[r].y);
             iacc[r][2 * m] = __vimin3_s32(iacc[r][2 * m], a0 + __float_as_int(bq[m].x), a1 + __float_as_int(bq[m].y));
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(256, 2) ubench_kpair(int64_t iters, void *sink
 
 extern "C" int apsp_ubench_minplus(int form, int64_t iters, int blocks, int threads, void *sink, void *stream,
                                    double *relax_per_s) {
-  if (!sink || !relax_per_s || iters <= 0 || form < 0 || form > 7) return APSP_EINVAL;
+  if (!sink || !relax_per_s || iters <= 0 || form < 0 || form > 8) return APSP_EINVAL;
   if (threads != 256) return APSP_EINVAL;  // the micro-tile layout is fixed
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (blocks <= 0) {
@@ -216,6 +228,7 @@ extern "C" int apsp_ubench_minplus(int form, int64_t iters, int blocks, int thre
       case 5: ubench_kpair<5><<<blocks, 256, 0, st>>>(its, sink); break;
       case 6: ubench_kpair<6><<<blocks, 256, 0, st>>>(its, sink); break;
       case 7: ubench_kpair<7><<<blocks, 256, 0, st>>>(its, sink); break;
+      case 8: ubench_kpair<8><<<blocks, 256, 0, st>>>(its, sink); break;
     }
   };
   launch(iters / 8 + 1);  // warm-up (clocks, instruction cache)
