@@ -286,13 +286,21 @@ int copy_matrix(void *dst, int64_t dld, const void *src, int64_t sld, int64_t n,
              : APSP_ECUDA;
 }
 
-// Delivers a finished request (s->mu held); frees it.
-int deliver(Server *s, Request *r, void *out, int64_t out_ld) {
+// Delivers a finished request and frees it.  Called with the lock `lk` on
+// s->mu held: the request leaves the table under the lock, its result is
+// copied out with the lock released (a large copy must not hold up the
+// scheduler or other waiters), and its staging buffer goes back to the pool
+// under the lock again.  Returns with the lock released.
+int deliver(Server *s, Request *r, void *out, int64_t out_ld, std::unique_lock<std::mutex> &lk) {
   int rc = r->state.load() == kDone ? APSP_OK : r->status;
+  s->table.erase(r->id);
+  lk.unlock();
   if (rc == APSP_OK && out && r->n > 0)
     rc = copy_matrix(out, out_ld, r->host, r->ld, r->n, esize(r->dtype), on_device(out));
-  if (r->host) s->pinned_free.emplace(r->host_cap, r->host);
-  s->table.erase(r->id);
+  if (r->host) {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->pinned_free.emplace(r->host_cap, r->host);
+  }
   delete r;
   return rc;
 }
@@ -411,14 +419,14 @@ extern "C" int apsp_submit(apsp_server *h, const void *host_dist, int64_t n, int
 extern "C" int apsp_poll(apsp_server *h, uint64_t ticket, void *out_dist, int64_t out_ld) {
   if (!h) return APSP_EINVAL;
   Server *s = &h->s;
-  std::lock_guard<std::mutex> lk(s->mu);
+  std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->table.find(ticket);
   if (it == s->table.end()) return APSP_EINVAL;
   Request *r = it->second;
   const int st = r->state.load();
   if (st == kQueued || st == kRunning) return APSP_EPENDING;
   if (st == kDone && out_dist && out_ld < r->n) return APSP_EINVAL;
-  return deliver(s, r, out_dist, out_ld);
+  return deliver(s, r, out_dist, out_ld, lk);
 }
 
 extern "C" int apsp_wait(apsp_server *h, uint64_t ticket, void *out_dist, int64_t out_ld, int64_t timeout_us) {
@@ -434,7 +442,7 @@ extern "C" int apsp_wait(apsp_server *h, uint64_t ticket, void *out_dist, int64_
   else if (!s->done_cv.wait_for(lk, std::chrono::microseconds(timeout_us), finished))
     return APSP_ETIMEOUT;
   if (r->state.load() == kDone && out_dist && out_ld < r->n) return APSP_EINVAL;
-  return deliver(s, r, out_dist, out_ld);
+  return deliver(s, r, out_dist, out_ld, lk);
 }
 
 extern "C" int apsp_server_stats(apsp_server *h, apsp_stats *out, int reset) {
