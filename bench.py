@@ -175,13 +175,15 @@ def _peaks():
 
 
 KERNEL_SOURCES = ("fw_kernels.cuh", "tileset.h", "apsp_common.cuh")
+# the int16x2 kernels live in a header of their own on top of those
+KERNEL_SOURCES_BY_DTYPE = {"f32": KERNEL_SOURCES, "i32": KERNEL_SOURCES, "i16": KERNEL_SOURCES + ("fw_s16x2.cuh",)}
 
 
-def kernel_source_hash() -> str:
-    """sha256 over the device-code sources of the phase kernels."""
+def kernel_source_hash(dtype: str = "f32") -> str:
+    """sha256 over the device-code sources of the phase kernels of `dtype`."""
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES_BY_DTYPE[dtype]:
         h.update(open(os.path.join(ROOT, "paper_1001_4108_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -194,10 +196,10 @@ def _measured_traffic(dtype: str, n: int, s: int, tiles: float):
     if not os.path.exists(rec_path):
         return None
     rec = json.load(open(rec_path))
-    if kernel_source_hash() != rec.get("kernel_sources_sha256"):
-        return None
     e = rec.get(dtype)
-    if not e or e["s"] != s or n <= s:
+    if not e or kernel_source_hash(dtype) != e.get("kernel_sources_sha256"):
+        return None
+    if e["s"] != s or n <= s:
         return None
     return e["bytes_per_launch"] / e["tiles_per_launch"] * tiles
 

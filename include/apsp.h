@@ -395,7 +395,9 @@ APSP_API int apsp_selftest_wait(int64_t limit_ns, void *stream);
  *          6 fp32 two scalar adds + three-input min (two k's),
  *          7 fp32 forms 4 and 6 alternating by column,
  *          8 int32 additions three quarters as multiply-adds by a runtime 1
- *            (FMA pipe), one quarter as adds, + three-input DPX min.
+ *            (FMA pipe), one quarter as adds, + three-input DPX min,
+ *          9 int16x2 DPX add-min on the int16x2 phase-3 kernel's own
+ *            micro-tile (8 rows x 4 words, one 128-bit B load per k).
  *   iters  sweeps of the slice.
  *   blocks blocks to launch (<= 0: 2 per SM); threads must be 256.
  *   sink   device buffer of blocks*256 4-byte words (results are written so

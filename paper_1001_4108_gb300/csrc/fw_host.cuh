@@ -7,6 +7,7 @@
 #include "../../include/apsp.h"
 #include "apsp_internal.h"
 #include "fw_kernels.cuh"
+#include "fw_s16x2.cuh"
 
 #include <type_traits>
 

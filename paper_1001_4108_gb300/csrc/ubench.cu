@@ -98,6 +98,53 @@ __global__ void __launch_bounds__(256, 2) ubench_kstep(int64_t iters, T *sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// form 9: the int16x2 phase-3 loop as the kernel runs it: an 8 x 4 word
+// micro-tile (8 rows x 8 int16 columns), A k-quads of replicated words by
+// 128-bit loads, one 128-bit load of B (rows of 64 words) per k.
+__global__ void __launch_bounds__(256, 2) ubench_s16x2_narrow(int64_t iters, uint32_t *sink) {
+  constexpr int kWords = kCols / 2;  // a B row: 128 int16 columns
+  __shared__ __align__(16) uint32_t As[kRows * kKs];
+  __shared__ __align__(16) uint32_t Bs[kKs * kWords];
+  for (int i = threadIdx.x; i < kRows * kKs; i += blockDim.x) As[i] = fill<uint32_t>(i);
+  for (int i = threadIdx.x; i < kKs * kWords; i += blockDim.x) Bs[i] = fill<uint32_t>(i + 7);
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16, sw = ty & 7;
+  const uint32_t *A = As + ty * kKs;
+  const uint32_t *B = Bs + 4 * tx;
+  uint32_t acc[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = fill<uint32_t>(1000 + r + c);
+#pragma unroll 1
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll 2
+    for (int q = 0; q < kKs / 4; ++q) {
+      uint32_t a[8][4];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(A + 16 * r * kKs + ((q ^ sw) << 2));
+        a[r][0] = v.x; a[r][1] = v.y; a[r][2] = v.z; a[r][3] = v.w;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint4 bv = *reinterpret_cast<const uint4 *>(B + (4 * q + u) * kWords);
+        const uint32_t bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = relax_s16x2(acc[r][c], a[r][u], bb[c]);
+      }
+    }
+  }
+  uint32_t s = acc[0][0];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s = acc[r][c] < s ? acc[r][c] : s;
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // form 4: the packed fp32 loop: per k-pair, 8 (k, k+1) pairs of A (64-bit
 // loads) and 4 column-pair quads of the k-pair interleaved B (128-bit loads),
 // then acc <- min(acc, a_k + b_k, a_k' + b_k') with one add.f32x2 and one
@@ -203,7 +250,7 @@ __global__ void __launch_bounds__(256, 2) ubench_kpair(int64_t iters, void *sink
 
 extern "C" int apsp_ubench_minplus(int form, int64_t iters, int blocks, int threads, void *sink, void *stream,
                                    double *relax_per_s) {
-  if (!sink || !relax_per_s || iters <= 0 || form < 0 || form > 8) return APSP_EINVAL;
+  if (!sink || !relax_per_s || iters <= 0 || form < 0 || form > 9) return APSP_EINVAL;
   if (threads != 256) return APSP_EINVAL;  // the micro-tile layout is fixed
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (blocks <= 0) {
@@ -229,6 +276,7 @@ extern "C" int apsp_ubench_minplus(int form, int64_t iters, int blocks, int thre
       case 6: ubench_kpair<6><<<blocks, 256, 0, st>>>(its, sink); break;
       case 7: ubench_kpair<7><<<blocks, 256, 0, st>>>(its, sink); break;
       case 8: ubench_kpair<8><<<blocks, 256, 0, st>>>(its, sink); break;
+      case 9: ubench_s16x2_narrow<<<blocks, 256, 0, st>>>(its, (uint32_t *)sink); break;
     }
   };
   launch(iters / 8 + 1);  // warm-up (clocks, instruction cache)
@@ -243,7 +291,8 @@ extern "C" int apsp_ubench_minplus(int form, int64_t iters, int blocks, int thre
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != APSP_OK) return rc;
-  // relaxations per thread per sweep of the 32-k slice (int16x2: two per lane)
+  // relaxations per thread per sweep of the 32-k slice (int16x2: two per
+  // lane; form 9 holds 32 lanes per thread, the others 64)
   const double per_sweep = (form == 2 ? 2.0 : 1.0) * 64.0 * kKs;
   *relax_per_s = (double)blocks * 256.0 * per_sweep * (double)iters / (ms * 1e-3);
   return APSP_OK;

@@ -50,7 +50,11 @@ def test_traffic_record_scales_by_tiles_and_tracks_sources():
     rec = json.load(open(bench.os.path.join(bench.ROOT, "profiles", "traffic.json")))
     f = rec["f32"]
     per_tile = f["bytes_per_launch"] / f["tiles_per_launch"]
-    if bench.kernel_source_hash() == rec["kernel_sources_sha256"]:
+    # each dtype's entry names the sources it was taken with and their hash
+    for dt in ("f32", "i32", "i16"):
+        assert tuple(rec[dt]["kernel_sources"]) == tuple(
+            "paper_1001_4108_gb300/csrc/" + x for x in bench.KERNEL_SOURCES_BY_DTYPE[dt])
+    if bench.kernel_source_hash("f32") == f["kernel_sources_sha256"]:
         got = bench._measured_traffic("f32", 16384, 128, 15876)
         assert abs(got - per_tile * 15876) < 1.0
         # the record is for s = 128 only; no figure for another tile side or a single-tile matrix

@@ -608,10 +608,10 @@ def test_int16_large_vs_int32_and_dijkstra():
 
 
 @pytest.mark.parametrize("n", [5200, 6144])
-def test_int16_bulk_two_tiles_per_cta(n):
-    """s = 128 int16x2 bulk launches take two tiles per CTA (odd and even
-    tile counts, ragged and whole): identical to the int32 path, to the
-    reversed k order and to exact Dijkstra rows."""
+def test_int16_s128_bulk_odd_and_even_tile_counts(n):
+    """s = 128 int16x2 phase 3 (deferred C tile, TMA ring) at odd and even
+    tile counts per launch, ragged and whole: identical to the int32 path,
+    to the reversed k order and to exact Dijkstra rows."""
     w32 = inputs.int_graph(n, 0.05, 1, 3, seed=n)
     w16 = inputs.to_int16(w32)
     assert binding.query_config(n, binding.APSP_I16).kblock == 128
