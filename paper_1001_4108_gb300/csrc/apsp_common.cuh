@@ -122,14 +122,69 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   }
 }
 
-// After a wait gave up at slice s of a ring of `stages` mbarriers: records
-// the error and waits (bounded again) for the copies this CTA still has in
-// flight -- slices s .. min(s + stages, nsl) - 1 -- so that none lands in
-// shared memory after the CTA has left.  Called by the thread that issued
-// the copies.
+// After a wait gave up at slice s of a ring of `stages` mbarriers refilled
+// behind a CTA barrier: records the error and waits (bounded again) for the
+// copies this CTA still has in flight -- slices s .. min(s + stages, nsl) - 1
+// -- so that none lands in shared memory after the CTA has left.  Called by
+// the thread that issued the copies.
 __device__ __forceinline__ void give_up_and_drain(int *err, uint64_t *full, int s, int stages, int nsl) {
   atomicCAS(err, 0, (int)kDevTimeoutTma);
   for (int t = s; t < s + stages && t < nsl; ++t) mbar_wait_bounded(&full[t % stages], (t / stages) & 1);
+}
+
+// Release of the stages of a TMA ring without a CTA barrier per slice.
+// Every warp, once done with the slice in stage st, counts itself in; the
+// last of the CTA's warps refills the stage with the slice STAGES further
+// on.  So warps wait only for data, never for each other, and drift apart by
+// less than the ring's depth.  (A CTA barrier per slice instead left each
+// warp waiting for the slowest, and the SM's other CTA did not fill those
+// waits: the integer phase 3 ran about 4 % faster without it.)
+// Lives in shared memory; one thread initialises it before a CTA barrier.
+template <int STAGES>
+struct RingCtl {
+  int issued;        // slices issued so far; they go out in slice order
+  int abort;         // a wait gave up: no further refills
+  int rel[STAGES];   // warps done with the slice now in each stage
+};
+
+template <int STAGES>
+__device__ __forceinline__ void ring_ctl_init(RingCtl<STAGES> *c, int issued) {
+  c->issued = issued;
+  c->abort = 0;
+#pragma unroll
+  for (int s = 0; s < STAGES; ++s) c->rel[s] = 0;
+}
+
+// Called by every thread of the CTA after its last read of stage st.
+// refill() issues the next slice into the stage (one thread runs it).
+template <int STAGES, int NWARP, typename F>
+__device__ __forceinline__ void ring_release(RingCtl<STAGES> *c, int st, bool timed_out, F &&refill) {
+  asm volatile("" ::: "memory");
+  __syncwarp();  // the whole warp is done reading the stage
+  if ((threadIdx.x & 31) == 0) {
+    if (timed_out) {
+      atomicOr(&c->abort, 1);
+      __threadfence_block();  // seen by whichever warp counts itself in last
+    }
+    if (atomicAdd(&c->rel[st], 1) == NWARP - 1) {
+      atomicExch(&c->rel[st], 0);
+      if (atomicOr(&c->abort, 0) == 0) {
+        refill();
+        atomicAdd(&c->issued, 1);
+      }
+    }
+  }
+}
+
+// After a wait gave up (one thread, after a CTA barrier): records the error
+// and waits (bounded again) for the copies that can still be in flight --
+// the last slice issued into each stage -- so that none lands in shared
+// memory after the CTA has left.
+template <int STAGES>
+__device__ __forceinline__ void ring_drain(RingCtl<STAGES> *c, uint64_t *full, int *err) {
+  atomicCAS(err, 0, (int)kDevTimeoutTma);
+  const int ni = *reinterpret_cast<volatile int *>(&c->issued);
+  for (int g = ni > STAGES ? ni - STAGES : 0; g < ni; ++g) mbar_wait_bounded(&full[g % STAGES], (g / STAGES) & 1);
 }
 
 // 2-D tiled TMA load global -> shared, completion counted on an mbarrier.

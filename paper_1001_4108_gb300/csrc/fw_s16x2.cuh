@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
   uint64_t *cbar = full + P::STAGES;
 
   int *tile_ij = reinterpret_cast<int *>(cbar + 1);  // (It, Jt), reread after the main loop
+  RingCtl<P::STAGES> *ring = reinterpret_cast<RingCtl<P::STAGES> *>(tile_ij + 2);
 
   const int tid = threadIdx.x;
   const int tx = tid % G, ty = tid / G;
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
     for (int s = 0; s < P::STAGES; ++s) mbar_init(&full[s], 1);
     if (DEFER_C) mbar_init(cbar, 1);
     fence_mbar_init();
+    ring_ctl_init(ring, P::STAGES < P::NSL ? P::STAGES : P::NSL);
     tile_ij[0] = It;
     tile_ij[1] = Jt;
   }
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
   bool timed_out = false;
   for (int s = 0; s < P::NSL; ++s) {
     const int st = s % P::STAGES;
-    if (!mbar_wait_bounded(&full[st], (s / P::STAGES) & 1)) timed_out = true;
+    if (!timed_out && !mbar_wait_bounded(&full[st], (s / P::STAGES) & 1)) timed_out = true;
     const uint32_t *Bw = reinterpret_cast<const uint32_t *>(Bs + st * P::B_BYTES) + 4 * tx;  // row: S/2 words
 #pragma unroll
     for (int qi = 0; qi < KS / 4; ++qi) {
@@ -177,22 +179,23 @@ __global__ void __launch_bounds__(P3S16<S>::TPB, S == 128 ? 2 : 8)
           for (int m = 0; m < 4; ++m) acc[r][m] = __viaddmin_s16x2(a[r][u], bb[m], acc[r][m]);
       }
     }
-    if (__syncthreads_or(timed_out)) {
-      if (tid == 0) {
-        give_up_and_drain(err, full, s, P::STAGES, P::NSL);
-        if (DEFER_C) mbar_wait_bounded(cbar, 0);
-      }
-      return;
+    // the last warp done with stage st refills it (no CTA barrier per slice)
+    if (s + P::STAGES < P::NSL)
+      ring_release<P::STAGES, P::TPB / 32>(ring, st, timed_out, [&] { issue(s + P::STAGES, st); });
+  }
+  // one barrier per tile: every slice consumed, and (deferred form) the C
+  // tile arrived
+  const bool c_late = DEFER_C && !timed_out && !mbar_wait_bounded(cbar, 0);
+  if (__syncthreads_or(timed_out || c_late)) {
+    if (tid == 0) {
+      ring_drain(ring, full, err);
+      if (DEFER_C) mbar_wait_bounded(cbar, 0);
     }
-    if (tid == 0 && s + P::STAGES < P::NSL) issue(s + P::STAGES, st);
+    return;
   }
 
   if (DEFER_C) {
     // fold in the C tile (rows ty + G r, int16 columns 8 tx .. 8 tx + 7)
-    if (__syncthreads_or(!mbar_wait_bounded(cbar, 0))) {  // all slices were consumed: only C is in flight
-      if (tid == 0) atomicCAS(err, 0, (int)kDevTimeoutTma);
-      return;
-    }
     const int64_t vi0 = (int64_t)lds_volatile(tile_ij) * S, vj0 = (int64_t)lds_volatile(tile_ij + 1) * S;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
