@@ -51,6 +51,9 @@ def _args():
     ap.add_argument("--small", type=int, default=100, help="steps of the c1 / c3 timings; 0 = skip")
     ap.add_argument("--other-dtype", type=int, default=1,
                     help="also time the other 32-bit type (int32 beside fp32) at the same n; 0 = skip")
+    ap.add_argument("--int16-n", type=int, default=16000,
+                    help="also time the int16x2 path at this n (unit weights, the largest bound with "
+                         "(n-1) Wmax < 16383 at n near 16384); 0 = skip")
     return ap.parse_args()
 
 
@@ -149,6 +152,75 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm),
                 "power_w_max": max(power) if power else None}
+
+
+class NvmlClock:
+    """SM clock and clock-event reasons read in-process through NVML (one
+    light query per sample, read only) by a background thread: the per-step
+    clock record of the host-path timing.  An nvidia-smi sampler there cost
+    the step it landed in several ms (its query), which a per-step record
+    must not do.  Without NVML every reading is None."""
+
+    CLOCK_SM = 1  # nvmlClockType_t
+    # nvmlClocksEventReasons bits that mark a slowed run
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.gpu, self.period = gpu_index, period_ms / 1e3
+        self.samples = []
+        self._lib = self._dev = self._t = None
+        self._stop = threading.Event()
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            dev = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(dev)) != 0:
+                return
+            self._lib, self._dev, self._ct = lib, dev, ctypes
+            self._reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+        except (OSError, AttributeError):
+            self._lib = None
+
+    def read(self):
+        """(SM MHz, reason bits) now, or (None, None)."""
+        if self._lib is None:
+            return None, None
+        ct = self._ct
+        mhz, bits = ct.c_uint(), ct.c_ulonglong()
+        if self._lib.nvmlDeviceGetClockInfo(self._dev, self.CLOCK_SM, ct.byref(mhz)) != 0:
+            return None, None
+        if self._reasons_fn is None or self._reasons_fn(self._dev, ct.byref(bits)) != 0:
+            return float(mhz.value), None
+        return float(mhz.value), int(bits.value)
+
+    def _run(self):
+        while not self._stop.is_set():
+            mhz, bits = self.read()
+            self.samples.append((time.perf_counter(), mhz, bits))
+            self._stop.wait(self.period)
+
+    def start(self):
+        if self._lib is not None:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+
+    def window_mhz(self, t0: float, t1: float):
+        v = [m for t, m, _ in self.samples if t0 <= t <= t1 and m is not None]
+        return statistics.median(v) if v else None
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=2)
+        if self._lib is None:
+            return {"sm_mhz": None, "reasons": ["nvml unavailable"], "samples": 0}
+        sm = [m for _, m, _ in self.samples if m is not None]
+        reasons = sorted({nm for _, _, b in self.samples if b for bit, nm in self.REASONS.items() if b & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "reasons": reasons, "samples": len(sm),
+                "source": "NVML in-process, %d ms period" % round(self.period * 1e3)}
 
 
 def max_over_ranks(x: float, device: str) -> float:
@@ -623,12 +695,11 @@ def measure_single(a, dtype: str, n: int, steps: int, warmup: int, e2e_steps: in
             host.copy_(src)
             binding.apsp_fw_host(host)
         ts, windows = [], []
-        # one clock sample per second: the sampler's own driver queries stay
-        # out of most steps
-        e2e_sampler = ClockSampler(clock_gpu, period_ms=1000) if clock_gpu is not None else None
+        # SM clock per step from in-process NVML reads (an nvidia-smi query
+        # landing in a step slowed that step by several ms)
+        e2e_sampler = NvmlClock(clock_gpu) if clock_gpu is not None else None
         if e2e_sampler:
             e2e_sampler.start()
-            time.sleep(0.5)  # the first sample arrives after nvidia-smi starts
         for _ in range(e2e_steps):
             host.copy_(src)
             torch.cuda.synchronize()
@@ -641,6 +712,15 @@ def measure_single(a, dtype: str, n: int, steps: int, warmup: int, e2e_steps: in
         if e2e_sampler:
             e2e_clocks = e2e_sampler.stop()
             e2e_clocks["sm_mhz_per_step"] = [e2e_sampler.window_mhz(t0, t1) for t0, t1 in windows]
+        # give the pinned buffers back (the caching host allocator keeps them
+        # otherwise): host-path steps measured later in the same process were
+        # steadier with less pinned memory held
+        del host, src
+        import gc
+        gc.collect()
+        empty_host = getattr(torch._C, "_host_emptyCache", None)
+        if empty_host is not None:
+            empty_host()
         t_med = statistics.median(ts)
         e2e = {"value": world * relax_per_step / t_med, "unit": "relaxations/s",
                "h2d_bytes_per_step": n * n * es, "d2h_bytes_per_step": n * n * es,
@@ -772,6 +852,13 @@ def run_ours(a):
                             clock_gpu=local if rank == 0 else None, world=world)
         m2.pop("work"), m2.pop("pristine")
         torch.cuda.empty_cache()
+    # the packed int16x2 path at full size (its own workload: n = 16000)
+    m16, n16 = None, a.int16_n
+    if n16 > 0 and a.dtype != "i16":
+        m16 = measure_single(a, "i16", n16, a.steps, a.warmup, a.e2e_steps, seed=rank,
+                             clock_gpu=local if rank == 0 else None, world=world)
+        m16.pop("work"), m16.pop("pristine")
+        torch.cuda.empty_cache()
 
     if rank != 0:
         if world > 1:
@@ -784,7 +871,7 @@ def run_ours(a):
     # memory operands, every SM): the sustained ceiling of the form
     sink = torch.empty(sms * 2 * 256, dtype=torch.int32, device="cuda")
     forms = {"f32": 4, "i32": 0, "i16": 2}
-    ceiling = {dt: binding.ubench(forms[dt], 2000, sink) for dt in {a.dtype, other} if dt}
+    ceiling = {dt: binding.ubench(forms[dt], 2000, sink) for dt in {a.dtype, other, "i16" if m16 else None} if dt}
     total_ms = m["total_ms"]
     line = {
         "metric": "relaxations/s (n^3/t)", "value": m["value"], "unit": "relaxations/s",
@@ -816,6 +903,17 @@ def run_ours(a):
             "gpu_launches": (lambda k: None if k is None else a.steps * k)(
                 _launches_per_solve(n, c2.kblock, c2.rounds, c2.lookahead, other)),
             "clocks": m2["clocks"], "e2e": m2["e2e"],
+            "timing": "as the main line: CUDA events on the launching stream, input restore inside"}
+    if m16 is not None:
+        c16 = m16["cfg"]
+        line["int16x2"] = {
+            "workload": _workload_name("i16", n16), "n": n16, "value": m16["value"], "unit": "relaxations/s",
+            "ms_per_step": m16["total_ms"] / a.steps, "steps": a.steps, "warmup": a.warmup,
+            "kblock": c16.kblock, "rounds": c16.rounds,
+            "roofline": roofline_block("i16", n16, m16, sms, peaks, peak_kind, ceiling["i16"]),
+            "gpu_launches": (lambda k: None if k is None else a.steps * k)(
+                _launches_per_solve(n16, c16.kblock, c16.rounds, c16.lookahead, "i16")),
+            "clocks": m16["clocks"], "e2e": m16["e2e"],
             "timing": "as the main line: CUDA events on the launching stream, input restore inside"}
     if a.small > 0:
         line["small_configs"] = bench_small_configs(a.small)

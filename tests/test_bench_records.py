@@ -69,3 +69,20 @@ def test_traffic_record_scales_by_tiles_and_tracks_sources():
 def test_job_value_is_whole_job_throughput():
     assert bench.job_value(10.0, 4, 2.0) == 20.0
     assert bench.job_value(8.0, 1, 0.5) == 16.0
+
+
+def test_nvml_clock_record_and_fallback():
+    c = bench.NvmlClock(0)
+    if c._lib is None:  # no NVML here: every reading is None and the record says so
+        assert c.read() == (None, None)
+        rec = c.stop()
+        assert rec["sm_mhz"] is None and rec["reasons"] == ["nvml unavailable"]
+    # the record from planted samples: per-window medians and the slowdown bits
+    c = bench.NvmlClock(0)
+    c._lib = True  # as if loaded; no thread is started
+    c.samples = [(1.0, 2070.0, 0x0), (2.0, 1980.0, 0x4), (3.0, None, None), (4.0, 2070.0, 0x1)]
+    assert c.window_mhz(0.5, 2.5) == (2070.0 + 1980.0) / 2
+    assert c.window_mhz(2.5, 3.5) is None
+    rec = c.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]  # 0x1 (idle) is not a slowdown
