@@ -623,6 +623,24 @@ def test_int16_s128_bulk_odd_and_even_tile_counts(n):
     np.testing.assert_array_equal(d32[rows], oracle.dijkstra_rows_i32(w32, rows))
 
 
+def test_int16_bench_workload_n16000():
+    """The bench's int16x2 line at its own size (n = 16000, p = 0.1, unit
+    weights: the largest weight bound with (n - 1) Wmax < 16383), in the
+    launch configuration it times (s = 128, lookahead, library graph):
+    every entry equal to the int32 path's on the same graph, and sampled rows
+    equal to exact Dijkstra rows of the oracle."""
+    n = 16000
+    w32 = inputs.int_graph(n, 0.1, 1, max(1, 16382 // (n - 1)), seed=16000)
+    w16 = inputs.to_int16(w32)
+    cfg = binding.query_config(n, binding.APSP_I16)
+    assert cfg.kblock == 128 and cfg.lookahead == 1
+    d16 = gpu_solve(w16)
+    d32 = gpu_solve(w32)
+    np.testing.assert_array_equal(np.where(d16 == inputs.INF_I16, INF, d16.astype(np.int32)), d32)
+    rows = [0, 7777, n - 1]
+    np.testing.assert_array_equal(d32[rows], oracle.dijkstra_rows_i32(w32, rows))
+
+
 # --------------------------------------------------------------- host path ---
 
 def test_host_entry_point():
