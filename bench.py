@@ -251,12 +251,24 @@ KERNEL_SOURCES = ("fw_kernels.cuh", "tileset.h", "apsp_common.cuh")
 KERNEL_SOURCES_BY_DTYPE = {"f32": KERNEL_SOURCES, "i32": KERNEL_SOURCES, "i16": KERNEL_SOURCES + ("fw_s16x2.cuh",)}
 
 
+def _code_only(text: str) -> str:
+    """C++ source without its comments and blank lines (string literals in
+    these headers hold no comment markers), so that editing a comment does
+    not change the hash."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_source_hash(dtype: str = "f32") -> str:
-    """sha256 over the device-code sources of the phase kernels of `dtype`."""
+    """sha256 over the device code (comments left out) of the phase kernels
+    of `dtype`."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES_BY_DTYPE[dtype]:
-        h.update(open(os.path.join(ROOT, "paper_1001_4108_gb300", "csrc", f), "rb").read())
+        with open(os.path.join(ROOT, "paper_1001_4108_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()
 
 

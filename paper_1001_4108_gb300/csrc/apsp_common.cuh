@@ -168,10 +168,12 @@ __device__ __forceinline__ void ring_release(RingCtl<STAGES> *c, int st, bool ti
   }
 }
 
-// After a wait gave up (one thread, after a CTA barrier): records the error
-// and waits (bounded again) for the copies that can still be in flight --
-// the last slice issued into each stage -- so that none lands in shared
-// memory after the CTA has left.
+// After a wait gave up (one thread: after a CTA barrier, or lane 0 of a warp
+// that leaves on its own): records the error and waits (bounded again) for
+// the copies that can still be in flight -- the last slice issued into each
+// stage -- so that none lands in shared memory after the CTA has left.  (The
+// CTA's shared memory lives until its last warp leaves, and a warp leaves
+// only after waiting for every slice it read or draining like this.)
 template <int STAGES>
 __device__ __forceinline__ void ring_drain(RingCtl<STAGES> *c, uint64_t *full, int *err) {
   atomicCAS(err, 0, (int)kDevTimeoutTma);

@@ -86,3 +86,10 @@ def test_nvml_clock_record_and_fallback():
     rec = c.stop()
     assert rec["sm_mhz"] == 2070.0 and rec["samples"] == 3
     assert rec["reasons"] == ["sw_power_cap"]  # 0x1 (idle) is not a slowdown
+
+
+def test_source_hash_ignores_comments_only():
+    assert bench._code_only("int a; // note\n/* block\n comment */ int b;\n\n  // only a comment\n") == "int a;\n int b;"
+    # a changed statement changes the code text, a changed comment does not
+    assert bench._code_only("x = 1; // one") == bench._code_only("x = 1; // uno")
+    assert bench._code_only("x = 1;") != bench._code_only("x = 2;")
